@@ -1,0 +1,200 @@
+/*
+ * tt_svd.h -- C ABI of a single-GPU (GB300, sm_103a) TT-SVD engine.
+ *
+ * The engine computes the truncated tensor-train SVD of a dense tensor core by
+ * core, right to left, as in Alg. 2 (optimized TSQR TT-SVD, Sec. 3.1.2 of
+ * Roehrig-Zoellner, Thies, Basermann, "Performance of the low-rank tensor-train
+ * SVD (TT-SVD) for large dense tensors on modern multi-core CPUs"):
+ *   per step i = d..2:  R of a Q-less tall-skinny QR of the unfolding W^(i)
+ *   (blockwise Householder, Alg. 6, plus a reduction tree over the partial R
+ *   factors, Sec. 3.2); the small SVD of R (Eq. QR_trick); the rank choice of
+ *   Alg. 2 line 8; the core T^(i) from V (line 9); and the product W^(i) V_r
+ *   written as the next unfolding (line 11).
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ * - Tensors are dense and Fortran ordered (n_1 fastest, Sec. 3.1.2 "Memory
+ *   layout"), i.e. a C-ordered array of shape (n_d, ..., n_1).  No padding.
+ * - All data pointers are DEVICE pointers unless a parameter says "host".
+ *   The caller owns every buffer; the library never allocates device memory
+ *   in these calls (the serve entry points allocate inside their budget).
+ * - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL =
+ *   legacy default stream).  Results are valid after the stream synchronises.
+ * - Argument errors are detected on the host before anything is launched and
+ *   return TT_EINVAL (nothing is written).  CUDA launch errors return
+ *   TT_ECUDA.  Device-side failures set a status word in the workspace that
+ *   tt_last_device_status() reads back.  No kernel traps or asserts.
+ * - Cores are written in FP64 for both storage precisions: core i (1-based)
+ *   has shape (r_{i-1}, n_i, r_i) in Fortran order, r_0 = r_d = 1.
+ * - Maximum order d is TT_MAX_D.
+ */
+#ifndef TT_SVD_H
+#define TT_SVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TT_MAX_D 32
+
+typedef enum {
+  TT_OK = 0,
+  TT_EINVAL = 1,     /* bad argument (checked on the host, nothing launched) */
+  TT_ENOMEM = 2,     /* workspace too small / budget exceeded */
+  TT_ECUDA = 3,      /* a CUDA call failed */
+  TT_ETIMEOUT = 4,   /* a bounded device-side or host-side wait ran out */
+  TT_ENOTIMPL = 5,   /* combination not supported */
+  TT_ECANCELLED = 6, /* request cancelled (server shut down) */
+  TT_ENUMERIC = 7    /* device-side numerical failure: the Jacobi SVD hit its sweep
+                        limit or a singular value was not finite */
+} tt_status;
+
+/* Storage precision of the input tensor X.  TT_F64: FP64 tensor.  TT_F32: the
+ * FP32 form (FP32 storage, FP32 Householder panels and FP32 W*V_r; the R
+ * reduction tree, the small SVD and the rank choice run in FP64-class
+ * arithmetic).  */
+typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
+
+/* Internal arithmetic of the FP64 form.  TT_ARITH_DF: float-float (two FP32
+ * words, about 48 significant bits) for all bulk work -- GB300 runs FP32 FMAs
+ * about 70x faster than FP64 FMAs.  TT_ARITH_F64: native FP64 everywhere.
+ * TT_ARITH_AUTO = TT_ARITH_DF.  Ignored for TT_F32 inputs. */
+typedef enum { TT_ARITH_AUTO = 0, TT_ARITH_DF = 1, TT_ARITH_F64 = 2 } tt_arith;
+
+typedef struct {
+  tt_arith arith;      /* see tt_arith */
+  int no_elide;        /* 1: run every step even when V would be square (see tt_svd) */
+  int tsqr_ctas;       /* 0 = auto; else number of CTAs of the first TSQR level */
+} tt_opts;
+
+/* ---- sizing ---------------------------------------------------------------
+ * tt_query: bytes needed for all d cores together (worst case, each core
+ * r_{i-1} n_i r_i doubles with r_k = min(r_max, n_1..n_k, n_{k+1}..n_d)) and
+ * for the workspace of tt_svd with these arguments.  `n` is a host array of d
+ * positive extents.  Returns TT_EINVAL for d < 1, d > TT_MAX_D, n_i < 1,
+ * r_max < 1 or tol < 0. */
+tt_status tt_query(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
+                   size_t* core_bytes, size_t* work_bytes);
+
+/* Worst-case element count of each core (host array caps[d]) and of the
+ * sigma_out buffer (*sigma_count): sigma_out holds, for step i = d..2 in that
+ * order, min(rows_i, n_i r_i) singular values at offset
+ * (d - i) * (*sigma_stride). */
+tt_status tt_core_caps(int d, const int64_t* n, int r_max, int64_t* caps,
+                       int64_t* sigma_stride, int64_t* sigma_count);
+
+/* ---- the hot path -----------------------------------------------------------
+ * tt_svd: truncated TT-SVD of X (Alg. 2).
+ *   X          device, n_1*...*n_d elements of type dt, Fortran order, read only
+ *   r_max      maximal TT rank (>= 1)
+ *   tol        epsilon of Alg. 2: delta = tol / sqrt(d-1) * ||Sigma_first||_F
+ *              (line 7); tol = 0 disables tolerance truncation
+ *   cores_out  HOST array of d DEVICE pointers; core i receives
+ *              r_{i-1} * n_i * r_i doubles (caller-allocated, >= caps[i-1])
+ *   ranks_out  device int64[d+1]: r_0..r_d
+ *   sigma_out  optional (NULL) device doubles, layout of tt_core_caps; entries of
+ *              an elided step are set to NaN
+ *   err2_out   optional (NULL) device double: sum over all steps of the
+ *              discarded sigma^2 (the a-posteriori error bound squared)
+ *   work       device workspace of at least tt_query's work_bytes, 256-byte aligned
+ * Step elision: when tol == 0 and min(r_max, rows_i) >= n_i r_i, V would be a
+ * square orthogonal matrix; the step is skipped (core = identity, W^(i-1) is a
+ * view of W^(i)).  Ranks, later singular values and the approximation are
+ * unchanged; only the gauge of that core differs.  opts->no_elide disables it. */
+tt_status tt_svd(const void* X, tt_dtype dt, int d, const int64_t* n, int r_max, double tol,
+                 double* const* cores_out, int64_t* ranks_out, double* sigma_out,
+                 double* err2_out, void* work, size_t work_bytes, void* stream);
+
+/* tt_svd with options (opts may be NULL = defaults). */
+tt_status tt_svd_ex(const void* X, tt_dtype dt, int d, const int64_t* n, int r_max, double tol,
+                    double* const* cores_out, int64_t* ranks_out, double* sigma_out,
+                    double* err2_out, void* work, size_t work_bytes, void* stream,
+                    const tt_opts* opts);
+
+/* Reads the device status word left by the last tt_svd* call that used `work`
+ * (synchronising `stream` first).  TT_OK if no device-side failure was seen. */
+tt_status tt_last_device_status(const void* work, void* stream);
+
+/* ---- building blocks (each one step of the path; used by the tests) ---------
+ * tt_tsqr: R factor of the Q-less TSQR of W (rows x m, column-major, leading
+ *   dimension ld >= rows) -- Alg. 6 panels in a flat tree per warp (Sec. 3.2)
+ *   and further levels of the same kernel over the stacked partial R's.
+ *   R_out: device m*m doubles, column-major, upper triangular (R is unique up
+ *   to the signs of its rows).  dt = storage type of W.  work: tt_tsqr_query.
+ *   1 <= m <= 512. */
+tt_status tt_tsqr_query(int64_t rows, int m, tt_dtype dt, size_t* work_bytes);
+tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, double* R_out,
+                  void* work, size_t work_bytes, void* stream);
+
+/* tt_small_svd: R = U Sigma V^T for a square m x m matrix R (column-major,
+ *   device doubles) by one-sided Jacobi (Eq. QR_trick needs Sigma and V only).
+ *   sigma: device m doubles, descending.  V: device m*m doubles, column-major.
+ *   work: tt_small_svd_query.  1 <= m <= 512. */
+tt_status tt_small_svd_query(int m, size_t* work_bytes);
+tt_status tt_small_svd(const double* R, int m, double* sigma, double* V, void* work,
+                       size_t work_bytes, void* stream);
+
+/* tt_tsmm: Y = W V (Sec. 4.1.2 TSMM; with the unpadded layouts used here the
+ *   reshape of Alg. 2 line 11 is a view of Y).  W: rows x m (ld), storage dt;
+ *   V: device m x k doubles column-major (ldv = m); Y: device rows x k doubles
+ *   column-major with leading dimension ldy >= rows.  Arithmetic as the
+ *   matching tt_svd form (float-float for TT_F64, FP32 for TT_F32). */
+tt_status tt_tsmm(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, const double* V,
+                  int k, double* Y, int64_t ldy, void* stream);
+
+/* tt_gen_uniform: entries start..start+count-1 of the i.i.d. uniform[0,1)
+ *   stream of `seed` (Philox4x32-10, Salmon et al. SC'11; entry e is built from
+ *   block e/2 with counter (lo32(e/2), hi32(e/2), 0, 0) and key (lo32(seed),
+ *   hi32(seed)); a double from words x, y is ((x>>5)*2^26 + (y>>6)) * 2^-53).
+ *   dt = TT_F64 writes doubles, TT_F32 writes the same values rounded to float. */
+tt_status tt_gen_uniform(void* out, tt_dtype dt, int64_t count, uint64_t seed, int64_t start,
+                         void* stream);
+
+/* ---- batched form -----------------------------------------------------------
+ * Many independent TT-SVDs in one call (same semantics as tt_svd per job). */
+typedef struct {
+  const void* X;            /* device input, Fortran order */
+  tt_dtype dtype;
+  int d;
+  int64_t n[TT_MAX_D];
+  int r_max;
+  double tol;
+  double* cores_out[TT_MAX_D];  /* device pointers, caps from tt_core_caps */
+  int64_t* ranks_out;       /* device int64[d+1] */
+  double* sigma_out;        /* optional */
+  double* err2_out;         /* optional */
+} tt_job;
+
+tt_status tt_batched_query(int batch, const tt_job* jobs, size_t* work_bytes);
+tt_status tt_svd_batched(int batch, const tt_job* jobs, void* work, size_t work_bytes,
+                         void* stream);
+
+/* ---- serve form -------------------------------------------------------------
+ * Continuous batching: requests are admitted while others run, as HBM budget
+ * and slots free up.  The server owns its workspace (allocated inside
+ * hbm_budget_bytes at creation); job inputs and outputs stay caller-owned. */
+typedef struct tt_server tt_server;
+typedef struct {
+  int max_inflight;         /* concurrent jobs on the device (slots) */
+  int n_streams;            /* CUDA streams used for overlap */
+  double timeout_s;         /* per-request limit for tt_serve_poll (0 = none) */
+} tt_serve_opts;
+typedef struct {
+  tt_status status;
+  double t_submit, t_start, t_done;   /* host clock seconds (steady clock) */
+} tt_job_result;
+
+tt_status tt_serve_create(size_t hbm_budget_bytes, const tt_serve_opts* opts, tt_server** out);
+tt_status tt_serve_submit(tt_server* s, const tt_job* job, uint64_t* ticket);
+tt_status tt_serve_poll(tt_server* s, uint64_t ticket, int wait, tt_job_result* out);
+tt_status tt_serve_destroy(tt_server* s);
+
+const char* tt_status_str(tt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TT_SVD_H */

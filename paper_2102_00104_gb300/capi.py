@@ -1,0 +1,172 @@
+"""ctypes binding of libttsvd.so: the C ABI of include/tt_svd.h, argument marshalling only.
+
+Every function here has the name and argument order of the C entry point.  The
+library is loaded on first use; if it is missing (not built) loading raises
+RuntimeError -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libttsvd.so")
+
+TT_MAX_D = 32
+STATUS = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENOMEM", 3: "TT_ECUDA", 4: "TT_ETIMEOUT",
+          5: "TT_ENOTIMPL", 6: "TT_ECANCELLED", 7: "TT_ENUMERIC"}
+TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_ETIMEOUT, TT_ENOTIMPL, TT_ECANCELLED, TT_ENUMERIC = range(8)
+TT_F64, TT_F32 = 0, 1
+TT_ARITH_AUTO, TT_ARITH_DF, TT_ARITH_F64 = 0, 1, 2
+
+# every symbol the header declares (checked by the CPU test suite)
+EXPORTED = ["tt_query", "tt_core_caps", "tt_svd", "tt_svd_ex", "tt_last_device_status",
+            "tt_tsqr_query", "tt_tsqr", "tt_small_svd_query", "tt_small_svd", "tt_tsmm",
+            "tt_gen_uniform", "tt_batched_query", "tt_svd_batched", "tt_serve_create",
+            "tt_serve_submit", "tt_serve_poll", "tt_serve_destroy", "tt_status_str"]
+
+
+class tt_opts(C.Structure):
+    _fields_ = [("arith", C.c_int), ("no_elide", C.c_int), ("tsqr_ctas", C.c_int)]
+
+
+class tt_job(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("dtype", C.c_int), ("d", C.c_int),
+                ("n", C.c_int64 * TT_MAX_D), ("r_max", C.c_int), ("tol", C.c_double),
+                ("cores_out", C.c_void_p * TT_MAX_D), ("ranks_out", C.c_void_p),
+                ("sigma_out", C.c_void_p), ("err2_out", C.c_void_p)]
+
+
+class tt_serve_opts(C.Structure):
+    _fields_ = [("max_inflight", C.c_int), ("n_streams", C.c_int), ("timeout_s", C.c_double)]
+
+
+class tt_job_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double)]
+
+
+class TTError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+_lib = None
+
+_SIGS = {
+    "tt_query": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p]),
+    "tt_core_caps": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tt_svd": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_void_p,
+                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "tt_svd_ex": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_void_p,
+                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
+                            C.c_void_p]),
+    "tt_last_device_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tt_tsqr_query": (C.c_int, [C.c_int64, C.c_int, C.c_int, C.c_void_p]),
+    "tt_tsqr": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_int64, C.c_void_p, C.c_void_p,
+                          C.c_size_t, C.c_void_p]),
+    "tt_small_svd_query": (C.c_int, [C.c_int, C.c_void_p]),
+    "tt_small_svd": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                               C.c_void_p]),
+    "tt_tsmm": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_int64, C.c_void_p, C.c_int,
+                          C.c_void_p, C.c_int64, C.c_void_p]),
+    "tt_gen_uniform": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_int64, C.c_void_p]),
+    "tt_batched_query": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
+    "tt_svd_batched": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "tt_serve_create": (C.c_int, [C.c_size_t, C.c_void_p, C.c_void_p]),
+    "tt_serve_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tt_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.c_void_p]),
+    "tt_serve_destroy": (C.c_int, [C.c_void_p]),
+    "tt_status_str": (C.c_char_p, [C.c_int]),
+}
+
+
+def lib(path: str | None = None):
+    """Load libttsvd.so once (raises RuntimeError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with paper_2102_00104_gb300.build.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    L = C.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(code: int, where: str) -> None:
+    if code != TT_OK:
+        raise TTError(code, where)
+
+
+def i64_array(vals):
+    arr = (C.c_int64 * max(1, len(vals)))(*[int(v) for v in vals])
+    return arr
+
+
+def ptr_array(ptrs):
+    return (C.c_void_p * max(1, len(ptrs)))(*[C.c_void_p(int(p)) for p in ptrs])
+
+
+# ---- same-name wrappers ------------------------------------------------------------------
+def tt_query(d, n, r_max, tol, dt):
+    cb, wb = C.c_size_t(0), C.c_size_t(0)
+    check(lib().tt_query(d, i64_array(n), r_max, tol, dt, C.byref(cb), C.byref(wb)), "tt_query")
+    return cb.value, wb.value
+
+
+def tt_core_caps(d, n, r_max):
+    caps = (C.c_int64 * d)()
+    ss, sc = C.c_int64(0), C.c_int64(0)
+    check(lib().tt_core_caps(d, i64_array(n), r_max, caps, C.byref(ss), C.byref(sc)), "tt_core_caps")
+    return list(caps), ss.value, sc.value
+
+
+def tt_svd(X_ptr, dt, d, n, r_max, tol, core_ptrs, ranks_ptr, sigma_ptr, err2_ptr, work_ptr,
+           work_bytes, stream=0, opts: tt_opts | None = None):
+    code = lib().tt_svd_ex(X_ptr, dt, d, i64_array(n), r_max, tol, ptr_array(core_ptrs), ranks_ptr,
+                           sigma_ptr, err2_ptr, work_ptr, work_bytes, stream,
+                           C.byref(opts) if opts is not None else None)
+    check(code, "tt_svd")
+
+
+def tt_last_device_status(work_ptr, stream=0):
+    return lib().tt_last_device_status(work_ptr, stream)
+
+
+def tt_tsqr_query(rows, m, dt):
+    wb = C.c_size_t(0)
+    check(lib().tt_tsqr_query(rows, m, dt, C.byref(wb)), "tt_tsqr_query")
+    return wb.value
+
+
+def tt_tsqr(W_ptr, dt, rows, m, ld, R_ptr, work_ptr, work_bytes, stream=0):
+    check(lib().tt_tsqr(W_ptr, dt, rows, m, ld, R_ptr, work_ptr, work_bytes, stream), "tt_tsqr")
+
+
+def tt_small_svd_query(m):
+    wb = C.c_size_t(0)
+    check(lib().tt_small_svd_query(m, C.byref(wb)), "tt_small_svd_query")
+    return wb.value
+
+
+def tt_small_svd(R_ptr, m, sigma_ptr, V_ptr, work_ptr, work_bytes, stream=0):
+    check(lib().tt_small_svd(R_ptr, m, sigma_ptr, V_ptr, work_ptr, work_bytes, stream), "tt_small_svd")
+
+
+def tt_tsmm(W_ptr, dt, rows, m, ld, V_ptr, k, Y_ptr, ldy, stream=0):
+    check(lib().tt_tsmm(W_ptr, dt, rows, m, ld, V_ptr, k, Y_ptr, ldy, stream), "tt_tsmm")
+
+
+def tt_gen_uniform(out_ptr, dt, count, seed, start=0, stream=0):
+    check(lib().tt_gen_uniform(out_ptr, dt, count, seed, start, stream), "tt_gen_uniform")
+
+
+def tt_status_str(code):
+    return lib().tt_status_str(code).decode()

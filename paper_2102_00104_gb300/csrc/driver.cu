@@ -1,0 +1,515 @@
+// driver.cu -- host side of the engine: planning, workspace layout, the step
+// loop of Alg. 2 and the C ABI declared in include/tt_svd.h.
+//
+// Step i (d..2) of Alg. 2 on one stream, with every data-dependent size kept in
+// device memory (DevState) so nothing waits for the host:
+//   TSQR levels (line 5) -> Jacobi SVD of R (line 6) -> rank choice (lines 7-8)
+//   -> core T^(i) from V (line 9) -> W^(i-1) = W^(i) V_r (line 11)
+// and at the end T^(1) = W^(1) (line 13).  Grids are sized for the worst-case
+// rank r_k = min(r_max, n_1..n_k, n_{k+1}..n_d).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "engine.h"
+#include "tt_svd.h"
+
+namespace tt {
+
+static int g_nsm = 0;
+static size_t g_smem_optin = 0;
+static std::mutex g_props_mu;
+
+static void load_props() {
+  std::lock_guard<std::mutex> lk(g_props_mu);
+  if (g_nsm) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) {
+    g_nsm = p.multiProcessorCount;
+    g_smem_optin = p.sharedMemPerBlockOptin;
+  } else {
+    g_nsm = 152;
+    g_smem_optin = 227 * 1024;
+  }
+}
+int num_sms() { load_props(); return g_nsm; }
+size_t max_smem_optin() { load_props(); return g_smem_optin; }
+
+static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---- TSQR plan --------------------------------------------------------------------
+static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, bool first,
+                            int nsm, int64_t ctas_override) {
+  TsqrLevel L{};
+  L.rows = rows;
+  L.mmax = m_max;
+  L.mval = m_max;
+  L.mb = m_max;
+  L.in = in;
+  L.comp = comp;
+  L.out = out;
+  int64_t warps_cap;
+  if (m_max <= 16) {
+    L.kind = 0;
+    L.maxm = m_max <= 4 ? 4 : (m_max <= 8 ? 8 : 16);
+    L.pr = 32 * (64 / L.maxm);
+    L.smem = 0;
+    warps_cap = (int64_t)nsm * 2 * 4;
+  } else {
+    L.kind = 1;
+    int nch = 1;
+    while (32 * nch < m_max) nch *= 2;
+    L.maxm = 32 * nch;
+    const size_t es = fmt_bytes(comp);
+    const int mstr = m_max | 1;
+    const size_t budget = 200 * 1024;
+    int nw = 4, pr = 128;
+    bool ok = false;
+    for (int w = 4; w >= 1 && !ok; w /= 2)
+      for (int p = 128; p >= 32 && !ok; p /= 2)
+        if ((size_t)w * p * mstr * es <= budget) { nw = w; pr = p; ok = true; }
+    if (!ok) { nw = 1; pr = 32; }
+    L.pr = pr;
+    L.nw = nw;
+    L.smem = (size_t)nw * pr * mstr * es;
+    const int per_sm = L.smem <= 100 * 1024 ? 2 : 1;
+    warps_cap = (int64_t)nsm * per_sm * nw;
+  }
+  L.panels = (rows + L.pr - 1) / L.pr;
+  int64_t warps;
+  if (first) {
+    warps = std::min<int64_t>(L.panels, warps_cap);
+    if (ctas_override > 0) warps = std::min<int64_t>(L.panels, ctas_override * (L.kind ? L.nw : 4));
+  } else {
+    warps = std::max<int64_t>(1, std::min<int64_t>(warps_cap, (L.panels + 7) / 8));
+  }
+  if (warps < 1) warps = 1;
+  const int nwmax = L.kind == 0 ? 4 : L.nw;
+  L.nw = (int)std::min<int64_t>(nwmax, warps);
+  L.ctas = (warps + L.nw - 1) / L.nw;
+  L.warps = L.ctas * L.nw;
+  return L;
+}
+
+static std::vector<TsqrLevel> plan_tsqr(int64_t rows, int m_max, Fmt in, Fmt comp1, Fmt comp2,
+                                        int nsm, int64_t ctas_override) {
+  std::vector<TsqrLevel> lv;
+  Fmt cur = in;
+  int64_t r = rows;
+  bool first = true;
+  for (int guard = 0; guard < 16; ++guard) {
+    const Fmt comp = first ? comp1 : comp2;
+    const Fmt out = comp;  // partial R's are stored in the arithmetic of their level
+    TsqrLevel L = make_level(r, m_max, cur, comp, out, first, nsm, ctas_override);
+    lv.push_back(L);
+    if (L.warps == 1) break;
+    r = L.warps * L.mb;
+    cur = out;
+    first = false;
+  }
+  return lv;
+}
+
+// ---- whole-call plan -----------------------------------------------------------------
+struct StepPlan {
+  int i;
+  int64_t rows;
+  int m_max;
+  int r_max_out;
+  bool elide;
+  Fmt in_fmt;
+  int out_buf;   // -1: none (elided)
+  std::vector<TsqrLevel> levels;
+  TsmmCfg tsmm;
+};
+
+struct Plan {
+  int d;
+  int64_t n[TT_MAX_D];
+  int r_max;
+  double tol;
+  tt_dtype dt;
+  Fmt xfmt, inter, comp_tsqr1, comp_tsqr2, comp_svd, comp_tsmm;
+  std::vector<StepPlan> steps;
+  int r_worst[TT_MAX_D + 1];
+  // workspace offsets
+  size_t off_state, off_W[2], off_R[2], off_Rscr, off_A, off_V, off_Vout, off_sig, total;
+  size_t szW[2], szR, szRscr, szJ, szVout;
+  int ldA, m_all_max;
+};
+
+static void worst_ranks(int d, const int64_t* n, int r_max, int* r) {
+  r[0] = 1;
+  r[d] = 1;
+  for (int k = 1; k < d; ++k) {
+    double left = 1, right = 1;
+    for (int a = 0; a < k; ++a) left *= (double)n[a];
+    for (int a = k; a < d; ++a) right *= (double)n[a];
+    double v = std::min<double>((double)r_max, std::min(left, right));
+    r[k] = (int)v;
+  }
+}
+
+static tt_status validate(int d, const int64_t* n, int r_max, double tol) {
+  if (d < 1 || d > TT_MAX_D || !n || r_max < 1 || !(tol >= 0.0) || !std::isfinite(tol))
+    return TT_EINVAL;
+  double total = 1;
+  for (int i = 0; i < d; ++i) {
+    if (n[i] < 1) return TT_EINVAL;
+    total *= (double)n[i];
+  }
+  if (total > 9.0e18) return TT_EINVAL;
+  return TT_OK;
+}
+
+static tt_status build_plan(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
+                            const tt_opts* opts, Plan& P) {
+  tt_status st = validate(d, n, r_max, tol);
+  if (st != TT_OK) return st;
+  if (dt != TT_F64 && dt != TT_F32) return TT_EINVAL;
+  const tt_arith ar = opts ? opts->arith : TT_ARITH_AUTO;
+  const bool no_elide = opts && opts->no_elide;
+  const int64_t ctas_override = opts ? opts->tsqr_ctas : 0;
+  P.d = d;
+  for (int i = 0; i < d; ++i) P.n[i] = n[i];
+  P.r_max = r_max;
+  P.tol = tol;
+  P.dt = dt;
+  if (dt == TT_F32) {
+    P.xfmt = Fmt::F32; P.inter = Fmt::F32;
+    P.comp_tsqr1 = Fmt::F32; P.comp_tsqr2 = Fmt::DF; P.comp_svd = Fmt::DF; P.comp_tsmm = Fmt::F32;
+  } else if (ar == TT_ARITH_F64) {
+    P.xfmt = Fmt::F64; P.inter = Fmt::F64;
+    P.comp_tsqr1 = P.comp_tsqr2 = P.comp_svd = P.comp_tsmm = Fmt::F64;
+  } else {
+    P.xfmt = Fmt::F64; P.inter = Fmt::DF;
+    P.comp_tsqr1 = P.comp_tsqr2 = P.comp_svd = P.comp_tsmm = Fmt::DF;
+  }
+  worst_ranks(d, n, r_max, P.r_worst);
+  const int nsm = num_sms();
+  P.steps.clear();
+  int64_t nbar = 1;
+  for (int i = 0; i < d; ++i) nbar *= n[i];
+  int64_t rows = d >= 1 ? nbar / n[d - 1] : 1;
+  Fmt cur = P.xfmt;
+  int par = 0;
+  P.szW[0] = P.szW[1] = 0;
+  P.szR = 0;
+  P.szRscr = 0;
+  P.m_all_max = 1;
+  for (int i = d; i >= 2; --i) {
+    StepPlan S;
+    S.i = i;
+    S.rows = rows;
+    const int64_t m64 = n[i - 1] * (int64_t)P.r_worst[i];
+    if (m64 > kMaxM) return TT_ENOTIMPL;
+    S.m_max = (int)m64;
+    S.r_max_out = P.r_worst[i - 1];
+    S.elide = (tol == 0.0) && !no_elide && std::min<int64_t>(r_max, rows) >= S.m_max;
+    S.in_fmt = cur;
+    S.out_buf = -1;
+    P.m_all_max = std::max(P.m_all_max, S.m_max);
+    if (!S.elide) {
+      S.levels = plan_tsqr(rows, S.m_max, cur, P.comp_tsqr1, P.comp_tsqr2, nsm, ctas_override);
+      for (auto& L : S.levels) {
+        P.szR = std::max(P.szR, (size_t)L.warps * L.mb * S.m_max * fmt_bytes(L.out));
+        P.szRscr = std::max(P.szRscr, tsqr_wide_scratch_bytes(L));
+      }
+      S.tsmm = plan_tsmm(cur, P.comp_tsmm, P.comp_svd, P.inter, S.m_max, S.r_max_out, rows, nsm);
+      S.out_buf = par;
+      P.szW[par] = std::max(P.szW[par], (size_t)rows * S.r_max_out * fmt_bytes(P.inter));
+      par ^= 1;
+      cur = P.inter;
+    }
+    P.steps.push_back(S);
+    rows /= n[i - 2];
+  }
+  const int mp = P.m_all_max + (P.m_all_max & 1);
+  P.ldA = mp;
+  P.szJ = jacobi_scratch_bytes(P.comp_svd, P.m_all_max);
+  P.szVout = (size_t)mp * mp * fmt_bytes(P.comp_svd);
+  size_t off = 0;
+  P.off_state = off; off += align256(sizeof(DevState));
+  P.off_W[0] = off; off += align256(P.szW[0]);
+  P.off_W[1] = off; off += align256(P.szW[1]);
+  P.off_R[0] = off; off += align256(P.szR);
+  P.off_R[1] = off; off += align256(P.szR);
+  P.off_Rscr = off; off += align256(P.szRscr);
+  P.off_A = off; off += align256(P.szJ);
+  P.off_V = P.off_A + P.szJ / 2;
+  P.off_Vout = off; off += align256(P.szVout);
+  P.off_sig = off; off += align256((size_t)mp * sizeof(double));
+  P.total = off;
+  return TT_OK;
+}
+
+static tt_status cuda_err(cudaError_t e) { return e == cudaSuccess ? TT_OK : TT_ECUDA; }
+#define TT_CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return TT_ECUDA; } while (0)
+
+static void sigma_layout(int d, const int64_t* n, const int* rw, int64_t* stride, int64_t* count) {
+  int64_t s = 1;
+  int64_t rows = 1;
+  for (int a = 0; a < d - 1; ++a) rows *= n[a];
+  for (int i = d; i >= 2; --i) {
+    const int64_t m = n[i - 1] * (int64_t)rw[i];
+    s = std::max<int64_t>(s, std::min<int64_t>(m, rows));
+    rows /= n[i - 2];
+  }
+  *stride = s;
+  *count = s * std::max(d - 1, 0);
+}
+
+static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out,
+                          int64_t* ranks_out, double* sigma_out, double* err2_out, void* work,
+                          cudaStream_t s) {
+  char* wb = static_cast<char*>(work);
+  DevState* st = reinterpret_cast<DevState*>(wb + P.off_state);
+  int* status = &st->status;
+  const int d = P.d;
+  int64_t sig_stride = 0, sig_count = 0;
+  sigma_layout(d, P.n, P.r_worst, &sig_stride, &sig_count);
+  TT_CK(launch_init_state(st, d, P.n, s));
+  const void* cur = X;
+  Fmt cur_fmt = P.xfmt;
+  int64_t rows = 1;
+  for (int a = 0; a < d - 1; ++a) rows *= P.n[a];
+  const double tol2 = (d > 1) ? P.tol * P.tol / (double)(d - 1) : 0.0;
+  for (const StepPlan& S : P.steps) {
+    const int i = S.i;
+    double* sig_step = sigma_out ? sigma_out + (int64_t)(d - i) * sig_stride : nullptr;
+    if (S.elide) {
+      TT_CK(launch_core_identity(S.m_max, cores_out[i - 1], s));
+      if (sig_step) TT_CK(launch_fill_nan(sig_step, sig_stride, s));
+      // record r_{i-1} = m_i and m_{i-1} = n_{i-1} m_i on the device
+      TT_CK(launch_set_rank(st, i, (int)P.n[i - 2], S.m_max, s));
+      rows /= P.n[i - 2];
+      continue;
+    }
+    // TSQR levels
+    const void* lin = cur;
+    int64_t lld = rows;
+    void* Rfin = nullptr;
+    int64_t ldRfin = 0;
+    Fmt rfmt = Fmt::DF;
+    for (size_t l = 0; l < S.levels.size(); ++l) {
+      const TsqrLevel& L = S.levels[l];
+      void* Rout = wb + P.off_R[l & 1];
+      const int64_t ldR = L.warps * L.mb;
+      TT_CK(launch_tsqr_level(L, lin, lld, &st->m[i], Rout, ldR, wb + P.off_Rscr, status, s));
+      lin = Rout;
+      lld = ldR;
+      Rfin = Rout;
+      ldRfin = ldR;
+      rfmt = L.out;
+    }
+    // small SVD of R
+    double* sig = reinterpret_cast<double*>(wb + P.off_sig);
+    void* Vout = wb + P.off_Vout;
+    TT_CK(launch_jacobi(P.comp_svd, rfmt, Rfin, ldRfin, &st->m[i], S.m_max, wb + P.off_A,
+                        wb + P.off_V, P.ldA, sig, Vout, P.ldA, status, s));
+    // rank choice, core
+    TT_CK(launch_truncate(sig, rows, i, (int)P.n[i - 2], P.r_max, tol2, st, sig_step, nullptr, s));
+    TT_CK(launch_core(P.comp_svd, Vout, P.ldA, st, i, cores_out[i - 1], s));
+    // W^(i-1) = W^(i) V_r
+    void* Y = wb + P.off_W[S.out_buf];
+    TT_CK(launch_tsmm(S.tsmm, cur, rows, rows, &st->m[i], Vout, P.ldA, &st->r[i - 1], Y, rows,
+                      status, s));
+    cur = Y;
+    cur_fmt = P.inter;
+    rows /= P.n[i - 2];
+  }
+  // T^(1) = W^(1): n_1 x r_1 (worst case converted; only r_0 n_1 r_1 entries are meaningful)
+  const int64_t cnt = P.n[0] * (int64_t)P.r_worst[1];
+  TT_CK(launch_convert_to_f64(cur_fmt, cur, cnt, cores_out[0], s));
+  TT_CK(launch_finish(st, d, ranks_out, err2_out, s));
+  return TT_OK;
+}
+
+}  // namespace tt
+
+using namespace tt;
+
+extern "C" {
+
+const char* tt_status_str(tt_status s) {
+  switch (s) {
+    case TT_OK: return "ok";
+    case TT_EINVAL: return "invalid argument";
+    case TT_ENOMEM: return "workspace too small or budget exceeded";
+    case TT_ECUDA: return "CUDA error";
+    case TT_ETIMEOUT: return "timed out";
+    case TT_ENOTIMPL: return "not implemented for these arguments";
+    case TT_ECANCELLED: return "cancelled";
+    case TT_ENUMERIC: return "numerical failure (no convergence or non-finite value)";
+  }
+  return "unknown status";
+}
+
+tt_status tt_query(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
+                   size_t* core_bytes, size_t* work_bytes) {
+  Plan P;
+  tt_status st = build_plan(d, n, r_max, tol, dt, nullptr, P);
+  if (st != TT_OK) return st;
+  if (core_bytes) {
+    size_t cb = 0;
+    for (int i = 1; i <= d; ++i) cb += (size_t)P.r_worst[i - 1] * n[i - 1] * P.r_worst[i] * 8;
+    *core_bytes = cb;
+  }
+  if (work_bytes) *work_bytes = P.total;
+  return TT_OK;
+}
+
+tt_status tt_core_caps(int d, const int64_t* n, int r_max, int64_t* caps, int64_t* sigma_stride,
+                       int64_t* sigma_count) {
+  tt_status st = validate(d, n, r_max, 0.0);
+  if (st != TT_OK) return st;
+  int rw[TT_MAX_D + 1];
+  worst_ranks(d, n, r_max, rw);
+  if (caps)
+    for (int i = 1; i <= d; ++i) caps[i - 1] = (int64_t)rw[i - 1] * n[i - 1] * rw[i];
+  int64_t a = 0, b = 0;
+  sigma_layout(d, n, rw, &a, &b);
+  if (sigma_stride) *sigma_stride = a;
+  if (sigma_count) *sigma_count = b;
+  return TT_OK;
+}
+
+tt_status tt_svd_ex(const void* X, tt_dtype dt, int d, const int64_t* n, int r_max, double tol,
+                    double* const* cores_out, int64_t* ranks_out, double* sigma_out,
+                    double* err2_out, void* work, size_t work_bytes, void* stream,
+                    const tt_opts* opts) {
+  if (!X || !cores_out || !work) return TT_EINVAL;
+  for (int i = 0; i < d && i < TT_MAX_D; ++i)
+    if (!cores_out[i]) return TT_EINVAL;
+  if (((uintptr_t)work & 255) != 0) return TT_EINVAL;
+  Plan P;
+  tt_status st = build_plan(d, n, r_max, tol, dt, opts, P);
+  if (st != TT_OK) return st;
+  if (work_bytes < P.total) return TT_ENOMEM;
+  return run_plan(P, X, cores_out, ranks_out, sigma_out, err2_out, work, (cudaStream_t)stream);
+}
+
+tt_status tt_svd(const void* X, tt_dtype dt, int d, const int64_t* n, int r_max, double tol,
+                 double* const* cores_out, int64_t* ranks_out, double* sigma_out,
+                 double* err2_out, void* work, size_t work_bytes, void* stream) {
+  return tt_svd_ex(X, dt, d, n, r_max, tol, cores_out, ranks_out, sigma_out, err2_out, work,
+                   work_bytes, stream, nullptr);
+}
+
+tt_status tt_last_device_status(const void* work, void* stream) {
+  if (!work) return TT_EINVAL;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return TT_ECUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, work, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TT_ECUDA;
+  if (v & DEV_ERR_SHAPE) return TT_EINVAL;
+  if (v & (DEV_SVD_NOCONV | DEV_NONFINITE)) return TT_ENUMERIC;
+  return TT_OK;
+}
+
+// ---- building blocks ------------------------------------------------------------------
+static Fmt tsqr_comp2(tt_dtype) { return Fmt::DF; }
+
+tt_status tt_tsqr_query(int64_t rows, int m, tt_dtype dt, size_t* work_bytes) {
+  if (rows < 1 || m < 1 || m > kMaxM || (dt != TT_F64 && dt != TT_F32) || !work_bytes)
+    return TT_EINVAL;
+  const Fmt in = dt == TT_F32 ? Fmt::F32 : Fmt::F64;
+  const Fmt c1 = dt == TT_F32 ? Fmt::F32 : Fmt::DF;
+  auto lv = plan_tsqr(rows, m, in, c1, tsqr_comp2(dt), num_sms(), 0);
+  size_t szR = 0, scr = 0;
+  for (auto& L : lv) {
+    szR = std::max(szR, (size_t)L.warps * L.mb * m * fmt_bytes(L.out));
+    scr = std::max(scr, tsqr_wide_scratch_bytes(L));
+  }
+  *work_bytes = align256(256) + 2 * align256(szR) + align256(scr);
+  return TT_OK;
+}
+
+tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, double* R_out,
+                  void* work, size_t work_bytes, void* stream) {
+  size_t need = 0;
+  tt_status st = tt_tsqr_query(rows, m, dt, &need);
+  if (st != TT_OK) return st;
+  if (!W || !R_out || !work || ld < rows || ((uintptr_t)work & 255)) return TT_EINVAL;
+  if (work_bytes < need) return TT_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Fmt in = dt == TT_F32 ? Fmt::F32 : Fmt::F64;
+  const Fmt c1 = dt == TT_F32 ? Fmt::F32 : Fmt::DF;
+  auto lv = plan_tsqr(rows, m, in, c1, tsqr_comp2(dt), num_sms(), 0);
+  size_t szR = 0;
+  for (auto& L : lv) szR = std::max(szR, (size_t)L.warps * L.mb * m * fmt_bytes(L.out));
+  char* wb = static_cast<char*>(work);
+  int* status = reinterpret_cast<int*>(wb);
+  TT_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+  char* R0 = wb + align256(256);
+  char* R1 = R0 + align256(szR);
+  char* scr = R1 + align256(szR);
+  const void* lin = W;
+  int64_t lld = ld;
+  void* Rfin = nullptr;
+  int64_t ldRfin = 0;
+  Fmt rf = Fmt::DF;
+  for (size_t l = 0; l < lv.size(); ++l) {
+    void* Rout = (l & 1) ? R1 : R0;
+    const int64_t ldR = lv[l].warps * lv[l].mb;
+    TT_CK(launch_tsqr_level(lv[l], lin, lld, nullptr, Rout, ldR, scr, status, s));
+    lin = Rout;
+    lld = ldR;
+    Rfin = Rout;
+    ldRfin = ldR;
+    rf = lv[l].out;
+  }
+  return cuda_err(launch_copy_mat_f64(rf, Rfin, ldRfin, m, m, 1, R_out, m, s));
+}
+
+tt_status tt_small_svd_query(int m, size_t* work_bytes) {
+  if (m < 1 || m > kMaxM || !work_bytes) return TT_EINVAL;
+  const int mp = m + (m & 1);
+  *work_bytes = align256(256) + align256(jacobi_scratch_bytes(Fmt::DF, m)) +
+                align256((size_t)mp * mp * fmt_bytes(Fmt::DF));
+  return TT_OK;
+}
+
+tt_status tt_small_svd(const double* R, int m, double* sigma, double* V, void* work,
+                       size_t work_bytes, void* stream) {
+  size_t need = 0;
+  tt_status st = tt_small_svd_query(m, &need);
+  if (st != TT_OK) return st;
+  if (!R || !sigma || !V || !work || ((uintptr_t)work & 255)) return TT_EINVAL;
+  if (work_bytes < need) return TT_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int mp = m + (m & 1);
+  char* wb = static_cast<char*>(work);
+  int* status = reinterpret_cast<int*>(wb);
+  TT_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+  char* A = wb + align256(256);
+  const size_t szJ = jacobi_scratch_bytes(Fmt::DF, m);
+  char* Vw = A + szJ / 2;
+  char* Vout = A + align256(szJ);
+  TT_CK(launch_jacobi(Fmt::DF, Fmt::F64, R, m, nullptr, m, A, Vw, mp, sigma, Vout, mp, status, s));
+  return cuda_err(launch_copy_mat_f64(Fmt::DF, Vout, mp, m, m, 0, V, m, s));
+}
+
+tt_status tt_tsmm(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, const double* V,
+                  int k, double* Y, int64_t ldy, void* stream) {
+  if (!W || !V || !Y || rows < 1 || m < 1 || m > kMaxM || k < 1 || k > m || ld < rows ||
+      ldy < rows || (dt != TT_F64 && dt != TT_F32))
+    return TT_EINVAL;
+  const Fmt in = dt == TT_F32 ? Fmt::F32 : Fmt::F64;
+  const Fmt comp = dt == TT_F32 ? Fmt::F32 : Fmt::DF;
+  TsmmCfg c = plan_tsmm(in, comp, Fmt::F64, Fmt::F64, m, k, rows, num_sms());
+  return cuda_err(launch_tsmm(c, W, rows, ld, nullptr, V, m, nullptr, Y, ldy, nullptr,
+                              (cudaStream_t)stream));
+}
+
+tt_status tt_gen_uniform(void* out, tt_dtype dt, int64_t count, uint64_t seed, int64_t start,
+                         void* stream) {
+  if (!out || count < 0 || start < 0 || (dt != TT_F64 && dt != TT_F32)) return TT_EINVAL;
+  return cuda_err(launch_gen_uniform(out, dt == TT_F32 ? Fmt::F32 : Fmt::F64, count, seed, start,
+                                     (cudaStream_t)stream));
+}
+
+}  // extern "C"

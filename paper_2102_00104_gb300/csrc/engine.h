@@ -1,0 +1,110 @@
+// engine.h -- internal interface between the host driver and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace tt {
+
+// element formats in device memory
+enum class Fmt : int { F64 = 0, DF = 1, F32 = 2 };
+inline size_t fmt_bytes(Fmt f) { return f == Fmt::F32 ? 4 : 8; }
+
+// device status word values (bit flags)
+enum : int {
+  DEV_OK = 0,
+  DEV_ERR_SHAPE = 1,      // a kernel saw a shape outside what it was launched for
+  DEV_SVD_NOCONV = 2,     // Jacobi SVD hit its sweep limit
+  DEV_NONFINITE = 4,      // a non-finite singular value appeared
+};
+
+// per-call device state (lives in the workspace)
+struct DevState {
+  int status;
+  int first_done;              // 1 once delta has been fixed (Alg. 2 line 7)
+  double delta2;
+  double err2;
+  int m[40];                   // m[i] = columns of W^(i) (1-based step index)
+  int r[40];                   // r[0..d]
+};
+
+constexpr int kMaxM = 512;     // widest unfolding handled
+
+// ---- TSQR ---------------------------------------------------------------------
+// One TSQR level: every warp runs a flat tree of Alg. 6 panels over its share of
+// the rows of W (rows x m, leading dimension ld, format in) and writes its R
+// (m x m, zero below the diagonal) as a block of `mb` rows of the stacked
+// column-major output (ldR = warps * mb rows).
+struct TsqrLevel {
+  int kind;          // 0 = narrow (register panels), 1 = wide (smem panels)
+  int maxm;          // narrow: 4/8/16 ; wide: 32*chunks (template bound)
+  int mmax;          // worst-case m of this level (<= maxm)
+  int mval;          // m passed by value when the device pointer is null
+  int mb;            // rows of one R block in the stacked output
+  int pr;            // panel rows per warp
+  int nw;            // warps per CTA
+  int64_t ctas;
+  int64_t warps;     // total warps = partial R count
+  int64_t rows;      // rows of this level's input
+  int64_t panels;
+  size_t smem;       // dynamic smem per CTA
+  Fmt in, comp, out;
+};
+
+cudaError_t launch_tsqr_level(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
+                              void* Rout, int64_t ldR, void* Rscr, int* status, cudaStream_t s);
+size_t tsqr_wide_scratch_bytes(const TsqrLevel& L);
+
+// ---- small SVD ------------------------------------------------------------------
+// One-sided Jacobi of the m x m matrix R (format rin, leading dimension ldR);
+// writes sigma (descending, FP64) and V (format comp, column-major, ldV).
+// m_dev may be null: then m = m_max.
+cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
+                          int m_max, void* Ag, void* Vg, int ldA, double* sigma, void* Vout,
+                          int ldV, int* status, cudaStream_t s);
+size_t jacobi_scratch_bytes(Fmt comp, int m_max);
+
+// ---- rank choice / cores --------------------------------------------------------
+cudaError_t launch_truncate(const double* sigma, int64_t rows, int step_i, int n_next,
+                            int r_max, double tol2_over_dm1, DevState* st,
+                            double* sigma_out_step, int64_t* ranks_out, cudaStream_t s);
+cudaError_t launch_core(Fmt vfmt, const void* V, int ldV, const DevState* st, int step_i,
+                        double* core, cudaStream_t s);
+cudaError_t launch_core_identity(int m, double* core, cudaStream_t s);
+cudaError_t launch_set_rank(DevState* st, int step_i, int n_next, int r, cudaStream_t s);
+// dst(i, k) = src(i, k) as FP64 for i < rows, k < cols (zero below the diagonal if upper)
+cudaError_t launch_copy_mat_f64(Fmt f, const void* src, int64_t lds, int rows, int cols, int upper,
+                                double* dst, int64_t ldd, cudaStream_t s);
+cudaError_t launch_convert_to_f64(Fmt f, const void* src, int64_t count, double* dst,
+                                  cudaStream_t s);
+cudaError_t launch_fill_nan(double* dst, int64_t count, cudaStream_t s);
+cudaError_t launch_init_state(DevState* st, int d, const int64_t* n_host, cudaStream_t s);
+cudaError_t launch_finish(const DevState* st, int d, int64_t* ranks_out, double* err2_out,
+                          cudaStream_t s);
+
+// ---- TSMM ----------------------------------------------------------------------
+// Y (rows x r, ldy, format out) = W (rows x m, ld, format in) * V(:, 0:r)
+// (V format vfmt, ldV); m = m_dev[0], r = r_dev[0]; comp = arithmetic.
+struct TsmmCfg {
+  Fmt in, comp, vfmt, out;
+  int m_max, r_max;
+  int tr;           // rows per tile
+  int mstr;         // smem row stride (elements)
+  size_t smem;
+  int64_t ctas;
+};
+TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int64_t rows,
+                  int num_sms);
+cudaError_t launch_tsmm(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
+                        const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
+                        int64_t ldy, int* status, cudaStream_t s);
+
+// ---- generator -------------------------------------------------------------------
+cudaError_t launch_gen_uniform(void* out, Fmt f, int64_t count, uint64_t seed, int64_t start,
+                               cudaStream_t s);
+
+// device properties (cached)
+int num_sms();
+size_t max_smem_optin();
+
+}  // namespace tt

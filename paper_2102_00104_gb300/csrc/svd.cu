@@ -1,0 +1,422 @@
+// svd.cu -- small SVD of R (Eq. QR_trick), the rank choice (Alg. 2 lines 7-8),
+// the core write (line 9), the last core (line 13) and small helpers.
+//
+// The SVD is one-sided Jacobi (Hestenes): columns of A = R are rotated in
+// pairs until they are mutually orthogonal; then sigma_j = ||a_j|| and the
+// accumulated rotations form V.  It works on R itself (never on R^T R), so
+// small singular values keep their accuracy.  Pairs follow the round-robin
+// (circle) ordering: m-1 rounds of m/2 disjoint pairs per sweep, one warp per
+// pair.  The rotation angle is taken from zeta = (beta - alpha) / (2 gamma)
+// with t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) (the 2x2 symmetric Schur
+// decomposition of [[alpha, gamma], [gamma, beta]]); t is formed in FP32 and
+// c = 1/sqrt(1+t^2), s = c t are then formed in the working arithmetic, so
+// each rotation is orthogonal to working precision even though its angle is
+// only FP32-accurate (the next sweep removes the remaining small coupling).
+#include "tsqr_kernels.cuh"
+
+namespace tt {
+
+namespace {
+
+__device__ __forceinline__ float fp32_hi(df a) { return a.hi; }
+__device__ __forceinline__ float fp32_hi(double a) { return (float)a; }
+__device__ __forceinline__ float fp32_hi(float a) { return a; }
+
+template <class C> __device__ __forceinline__ C scale_pow2(C a, int e);
+template <> __device__ __forceinline__ df scale_pow2<df>(df a, int e) {
+  return mkdf(ldexpf(a.hi, e), ldexpf(a.lo, e));
+}
+template <> __device__ __forceinline__ double scale_pow2<double>(double a, int e) { return ldexp(a, e); }
+
+template <class C> __device__ __forceinline__ C from_f32(float x);
+template <> __device__ __forceinline__ df from_f32<df>(float x) { return mkdf(x, 0.f); }
+template <> __device__ __forceinline__ double from_f32<double>(float x) { return (double)x; }
+
+template <class C> __device__ __forceinline__ float conv_tol();
+template <> __device__ __forceinline__ float conv_tol<df>() { return 2e-14f; }
+template <> __device__ __forceinline__ float conv_tol<double>() { return 1e-15f; }
+
+// one thread block; A, V in shared memory when `smem_ok`, else in global (Ag, Vg)
+template <class C, class RI>
+__global__ void __launch_bounds__(1024)
+k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, int m_max,
+         C* __restrict__ Ag, C* __restrict__ Vg, int ldA, int smem_ok, double* __restrict__ sigma,
+         C* __restrict__ Vout, int ldV, int* status, int max_sweeps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_rot;
+  __shared__ int s_exp;
+  __shared__ float s_red[32];
+  const int m = m_ptr ? *m_ptr : m_max;
+  if (m < 1 || m > m_max) {
+    if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
+    return;
+  }
+  const int mp = m + (m & 1);  // even count of columns (one zero column added for odd m)
+  C* A = smem_ok ? reinterpret_cast<C*>(smem_raw) : Ag;
+  C* V = smem_ok ? reinterpret_cast<C*>(smem_raw) + (size_t)ldA * mp : Vg;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nwarps = nt >> 5;
+
+  // exponent of max |R| for an exact power-of-two scaling (keeps squares in FP32 range)
+  float mx = 0.f;
+  for (int idx = tid; idx < m * m; idx += nt) {
+    const int i = idx % m, k = idx / m;
+    const float v = fabsf(fp32_hi(ld_as<C>(R[i + (int64_t)k * ldR])));
+    mx = fmaxf(mx, v);
+  }
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) s_red[wid] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < nwarps; ++w) t = fmaxf(t, s_red[w]);
+    int e = 0;
+    if (t > 0.f) frexpf(t, &e);
+    s_exp = e;
+  }
+  __syncthreads();
+  const int ex = s_exp;
+  for (int idx = tid; idx < ldA * mp; idx += nt) {
+    const int i = idx % ldA, k = idx / ldA;
+    C a = Tr<C>::zero();
+    if (i < m && k < m && i <= k) a = scale_pow2<C>(ld_as<C>(R[i + (int64_t)k * ldR]), -ex);
+    A[idx] = a;
+    V[idx] = (i == k) ? Tr<C>::one() : Tr<C>::zero();
+  }
+  __syncthreads();
+
+  const float tol = conv_tol<C>();
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < mp - 1; ++rnd) {
+      for (int slot = wid; slot < mp / 2; slot += nwarps) {
+        int p, q;
+        if (slot == 0) {
+          p = mp - 1;
+          q = rnd;
+        } else {
+          p = (rnd + slot) % (mp - 1);
+          q = (rnd - slot + mp - 1) % (mp - 1);
+        }
+        C* ap = A + (size_t)p * ldA;
+        C* aq = A + (size_t)q * ldA;
+        C al = Tr<C>::zero(), be = Tr<C>::zero(), ga = Tr<C>::zero();
+        for (int i = lane; i < m; i += 32) {
+          const C x = ap[i], y = aq[i];
+          al = fmac(x, x, al);
+          be = fmac(y, y, be);
+          ga = fmac(x, y, ga);
+        }
+        for (int o = 16; o; o >>= 1) {
+          al = add(al, shfl_xor(al, o));
+          be = add(be, shfl_xor(be, o));
+          ga = add(ga, shfl_xor(ga, o));
+        }
+        const float gf = fabsf(fp32_hi(ga));
+        const float nf = sqrtf(fp32_hi(al)) * sqrtf(fp32_hi(be));
+        if (gf > tol * nf && gf > 0.f) {
+          const C zeta = div_(sub(be, al), add(ga, ga));
+          const float zf = fp32_hi(zeta);
+          const float az = fabsf(zf);
+          float tf = az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f)));
+          if (zf < 0.f) tf = -tf;
+          const C t = from_f32<C>(tf);
+          const C c = div_(Tr<C>::one(), sqrt_(fmac(t, t, Tr<C>::one())));
+          const C s = mul(c, t);
+          for (int i = lane; i < m; i += 32) {
+            const C x = ap[i], y = aq[i];
+            ap[i] = fnmac(s, y, mul(c, x));
+            aq[i] = fmac(s, x, mul(c, y));
+          }
+          C* vp = V + (size_t)p * ldA;
+          C* vq = V + (size_t)q * ldA;
+          for (int i = lane; i < mp; i += 32) {
+            const C x = vp[i], y = vq[i];
+            vp[i] = fnmac(s, y, mul(c, x));
+            vq[i] = fmac(s, x, mul(c, y));
+          }
+          if (lane == 0) s_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) break;
+    __syncthreads();
+  }
+  if (sweep >= max_sweeps && tid == 0 && status) atomicOr(status, DEV_SVD_NOCONV);
+
+  // sigma_k = ||a_k||, sorted descending (stable by index); V columns follow
+  C* nrm = smem_ok ? V + (size_t)ldA * mp : reinterpret_cast<C*>(smem_raw);
+  for (int k = tid; k < m; k += nt) {
+    C nk = Tr<C>::zero();
+    const C* ak = A + (size_t)k * ldA;
+    for (int i = 0; i < m; ++i) nk = fmac(ak[i], ak[i], nk);
+    nrm[k] = nk;
+  }
+  __syncthreads();
+  for (int k = tid; k < m; k += nt) {
+    const C nk = nrm[k];
+    int rank = 0;
+    for (int k2 = 0; k2 < m; ++k2) {
+      if (k2 == k) continue;
+      const C n2 = nrm[k2];
+      if (is_gt(n2, nk) || (!is_gt(nk, n2) && k2 < k)) ++rank;
+    }
+    const double sg = ldexp(to_f64(sqrt_(nk)), ex);
+    if (!isfinite(sg) && status) atomicOr(status, DEV_NONFINITE);
+    sigma[rank] = sg;
+    const C* vk = V + (size_t)k * ldA;
+    for (int i = 0; i < m; ++i) Vout[i + (size_t)rank * ldV] = vk[i];
+  }
+}
+
+// ---- rank choice: Alg. 2 lines 7-8 --------------------------------------------
+__global__ void k_truncate(const double* __restrict__ sigma, int64_t rows, int step_i, int n_next,
+                           int r_max, double tol2_over_dm1, DevState* st,
+                           double* __restrict__ sigma_out, int64_t* __restrict__ ranks_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int m = st->m[step_i];
+  const int s = (int)((int64_t)m < rows ? m : rows);
+  double total = 0.0;
+  for (int k = s - 1; k >= 0; --k) total += sigma[k] * sigma[k];
+  if (!st->first_done) {
+    st->delta2 = tol2_over_dm1 * total;  // delta^2 = eps^2/(d-1) ||Sigma_first||_F^2
+    st->first_done = 1;
+  }
+  const double d2 = st->delta2;
+  int r_delta = s;
+  if (d2 > 0.0) {
+    // smallest j with sigma_{j+1}^2 + ... <= delta^2 (tail summed from the smallest value)
+    double tail = 0.0;
+    r_delta = s;
+    for (int j = s - 1; j >= 0; --j) {
+      const double nt = tail + sigma[j] * sigma[j];
+      if (nt <= d2) { r_delta = j; tail = nt; } else break;
+    }
+  }
+  int r = r_max;
+  if (r_delta < r) r = r_delta;
+  if (s < r) r = s;
+  if (r < 1) r = 1;
+  double disc = 0.0;
+  for (int k = s - 1; k >= r; --k) disc += sigma[k] * sigma[k];
+  st->err2 += disc;
+  st->r[step_i - 1] = r;
+  st->m[step_i - 1] = n_next * r;
+  if (sigma_out) for (int k = 0; k < s; ++k) sigma_out[k] = sigma[k];
+  if (ranks_out) ranks_out[step_i - 1] = r;
+}
+
+template <class C>
+__global__ void k_core(const C* __restrict__ V, int ldV, const DevState* st, int step_i,
+                       double* __restrict__ core) {
+  const int m = st->m[step_i];
+  const int r = st->r[step_i - 1];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)r * m;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx % r);
+    const int j = (int)(idx / r);
+    core[idx] = to_f64(V[j + (size_t)a * ldV]);  // T[a + r j] = V[j][a]
+  }
+}
+
+__global__ void k_set_rank(DevState* st, int step_i, int n_next, int r) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->r[step_i - 1] = r;
+  st->m[step_i - 1] = n_next * r;
+}
+
+template <class S>
+__global__ void k_copy_mat_f64(const S* __restrict__ src, int64_t lds, int rows, int cols,
+                               int upper, double* __restrict__ dst, int64_t ldd) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)rows * cols;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % rows), k = (int)(idx / rows);
+    double v = to_f64(ld_as<df>(src[i + k * lds]));
+    if (upper && i > k) v = 0.0;
+    dst[i + k * ldd] = v;
+  }
+}
+template <>
+__global__ void k_copy_mat_f64<double>(const double* __restrict__ src, int64_t lds, int rows,
+                                       int cols, int upper, double* __restrict__ dst, int64_t ldd) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)rows * cols;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % rows), k = (int)(idx / rows);
+    double v = src[i + k * lds];
+    if (upper && i > k) v = 0.0;
+    dst[i + k * ldd] = v;
+  }
+}
+
+__global__ void k_core_identity(int m, double* core) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)m * m;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    core[idx] = (idx % m == idx / m) ? 1.0 : 0.0;
+}
+
+template <class S>
+__global__ void k_to_f64(const S* __restrict__ src, int64_t count, double* __restrict__ dst) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < count;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    dst[idx] = to_f64(ld_as<df>(src[idx]));
+}
+template <>
+__global__ void k_to_f64<double>(const double* __restrict__ src, int64_t count, double* __restrict__ dst) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < count;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    dst[idx] = src[idx];
+}
+
+__global__ void k_fill_nan(double* dst, int64_t count) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < count;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    dst[idx] = __longlong_as_double(0x7FF8000000000000ll);
+}
+
+struct InitArgs {
+  int d;
+  int n[40];
+};
+
+__global__ void k_init_state(DevState* st, InitArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->status = 0;
+  st->first_done = 0;
+  st->delta2 = 0.0;
+  st->err2 = 0.0;
+  for (int i = 0; i < 40; ++i) { st->m[i] = 0; st->r[i] = 1; }
+  st->m[a.d] = a.n[a.d - 1];  // W^(d) has n_d columns (r_d = 1)
+}
+
+__global__ void k_finish(const DevState* st, int d, int64_t* ranks_out, double* err2_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (ranks_out) {
+    ranks_out[0] = 1;
+    ranks_out[d] = 1;
+    for (int i = 1; i < d; ++i) ranks_out[i] = st->r[i];
+  }
+  if (err2_out) *err2_out = st->err2;
+}
+
+inline unsigned grid_for(int64_t n, int bs) {
+  int64_t g = (n + bs - 1) / bs;
+  if (g < 1) g = 1;
+  if (g > 4096) g = 4096;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+size_t jacobi_scratch_bytes(Fmt comp, int m_max) {
+  const int mp = m_max + (m_max & 1);
+  return 2ull * mp * mp * fmt_bytes(comp);
+}
+
+cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
+                          int m_max, void* Ag, void* Vg, int ldA, double* sigma, void* Vout,
+                          int ldV, int* status, cudaStream_t s) {
+  const int mp = m_max + (m_max & 1);
+  const size_t need = 2ull * ldA * mp * fmt_bytes(comp);
+  const int smem_ok = need <= 200 * 1024 ? 1 : 0;
+  const size_t smem = (smem_ok ? need : 0) + (size_t)mp * fmt_bytes(comp);
+  int threads = 32 * ((mp / 2 + 0) > 32 ? 32 : (mp / 2 < 1 ? 1 : mp / 2));
+  if (threads < 64) threads = 64;
+  const int sweeps = 60;
+  if (comp == Fmt::DF && rin == Fmt::DF) {
+    auto k = k_jacobi<df, df>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<1, threads, smem, s>>>((const df*)R, ldR, m_dev, m_max, (df*)Ag, (df*)Vg, ldA, smem_ok,
+                               sigma, (df*)Vout, ldV, status, sweeps);
+  } else if (comp == Fmt::DF && rin == Fmt::F64) {
+    auto k = k_jacobi<df, double>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<1, threads, smem, s>>>((const double*)R, ldR, m_dev, m_max, (df*)Ag, (df*)Vg, ldA,
+                               smem_ok, sigma, (df*)Vout, ldV, status, sweeps);
+  } else if (comp == Fmt::DF && rin == Fmt::F32) {
+    auto k = k_jacobi<df, float>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<1, threads, smem, s>>>((const float*)R, ldR, m_dev, m_max, (df*)Ag, (df*)Vg, ldA,
+                               smem_ok, sigma, (df*)Vout, ldV, status, sweeps);
+  } else if (comp == Fmt::F64 && rin == Fmt::F64) {
+    auto k = k_jacobi<double, double>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<1, threads, smem, s>>>((const double*)R, ldR, m_dev, m_max, (double*)Ag, (double*)Vg,
+                               ldA, smem_ok, sigma, (double*)Vout, ldV, status, sweeps);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_truncate(const double* sigma, int64_t rows, int step_i, int n_next, int r_max,
+                            double tol2_over_dm1, DevState* st, double* sigma_out_step,
+                            int64_t* ranks_out, cudaStream_t s) {
+  k_truncate<<<1, 32, 0, s>>>(sigma, rows, step_i, n_next, r_max, tol2_over_dm1, st,
+                              sigma_out_step, ranks_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_core(Fmt vfmt, const void* V, int ldV, const DevState* st, int step_i,
+                        double* core, cudaStream_t s) {
+  if (vfmt == Fmt::DF)
+    k_core<df><<<64, 256, 0, s>>>((const df*)V, ldV, st, step_i, core);
+  else if (vfmt == Fmt::F64)
+    k_core<double><<<64, 256, 0, s>>>((const double*)V, ldV, st, step_i, core);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_rank(DevState* st, int step_i, int n_next, int r, cudaStream_t s) {
+  k_set_rank<<<1, 32, 0, s>>>(st, step_i, n_next, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_mat_f64(Fmt f, const void* src, int64_t lds, int rows, int cols, int upper,
+                                double* dst, int64_t ldd, cudaStream_t s) {
+  const unsigned g = grid_for((int64_t)rows * cols, 256);
+  if (f == Fmt::F64) k_copy_mat_f64<double><<<g, 256, 0, s>>>((const double*)src, lds, rows, cols, upper, dst, ldd);
+  else if (f == Fmt::DF) k_copy_mat_f64<df><<<g, 256, 0, s>>>((const df*)src, lds, rows, cols, upper, dst, ldd);
+  else k_copy_mat_f64<float><<<g, 256, 0, s>>>((const float*)src, lds, rows, cols, upper, dst, ldd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_core_identity(int m, double* core, cudaStream_t s) {
+  k_core_identity<<<grid_for((int64_t)m * m, 256), 256, 0, s>>>(m, core);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_to_f64(Fmt f, const void* src, int64_t count, double* dst,
+                                  cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const unsigned g = grid_for(count, 256);
+  if (f == Fmt::F64) k_to_f64<double><<<g, 256, 0, s>>>((const double*)src, count, dst);
+  else if (f == Fmt::DF) k_to_f64<df><<<g, 256, 0, s>>>((const df*)src, count, dst);
+  else k_to_f64<float><<<g, 256, 0, s>>>((const float*)src, count, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_nan(double* dst, int64_t count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_fill_nan<<<grid_for(count, 256), 256, 0, s>>>(dst, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(DevState* st, int d, const int64_t* n_host, cudaStream_t s) {
+  InitArgs a;
+  a.d = d;
+  for (int i = 0; i < 40; ++i) a.n[i] = i < d ? (int)n_host[i] : 0;
+  k_init_state<<<1, 32, 0, s>>>(st, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const DevState* st, int d, int64_t* ranks_out, double* err2_out,
+                          cudaStream_t s) {
+  k_finish<<<1, 32, 0, s>>>(st, d, ranks_out, err2_out);
+  return cudaGetLastError();
+}
+
+}  // namespace tt

@@ -1,0 +1,163 @@
+// tsmm.cu -- Y = W V(:, 0:r) (Alg. 2 line 11; TSMM of Sec. 4.1.2) and the
+// uniform[0,1) Philox4x32-10 input generator.
+//
+// W is rows x m column-major.  With the unpadded layouts used here the
+// reshape of line 11 is a view: the rows x r product, column-major with
+// leading dimension rows, is already W^(i-1) = rows/n_{i-1} x (n_{i-1} r).
+// A CTA stages a tile of `tr` rows x m of W in shared memory (row-major, odd
+// stride) with coalesced loads along the rows, V(:, 0:r) once per CTA, and
+// computes the tr x r outputs with consecutive threads on consecutive rows
+// (coalesced stores).
+#include "tsqr_kernels.cuh"
+
+namespace tt {
+
+namespace {
+
+template <class C, class S, class VS, class SO>
+__global__ void __launch_bounds__(256)
+k_tsmm(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
+       int m_val, const VS* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
+       SO* __restrict__ Y, int64_t ldy, int tr, int mstr, int m_max, int r_max, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = m_ptr ? *m_ptr : m_val;
+  const int r = r_ptr ? *r_ptr : r_val;
+  if (m < 1 || m > m_max || r < 1 || r > r_max || r > m) {
+    if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
+    return;
+  }
+  C* Vs = reinterpret_cast<C*>(smem_raw);            // Vs[k * r + c]
+  C* T = Vs + (size_t)m_max * r_max;                 // T[i * mstr + k]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < m * r; idx += nt) {
+    const int k = idx / r, c = idx % r;
+    Vs[idx] = ld_as<C>(V[k + (size_t)c * ldV]);
+  }
+  const int64_t ntiles = (rows + tr - 1) / tr;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * tr;
+    __syncthreads();
+    for (int idx = tid; idx < tr * m; idx += nt) {
+      const int i = idx % tr, k = idx / tr;
+      const int64_t row = r0 + i;
+      T[(size_t)i * mstr + k] = row < rows ? ld_as<C>(W[row + (int64_t)k * ld]) : Tr<C>::zero();
+    }
+    __syncthreads();
+    for (int idx = tid; idx < tr * r; idx += nt) {
+      const int i = idx % tr, c = idx / tr;
+      const int64_t row = r0 + i;
+      const C* ti = T + (size_t)i * mstr;
+      C acc = Tr<C>::zero();
+      for (int k = 0; k < m; ++k) acc = fmac(ti[k], Vs[k * r + c], acc);
+      if (row < rows) Y[row + (int64_t)c * ldy] = st_as<SO>(acc);
+    }
+  }
+}
+
+template <Fmt F> using T_ = typename FT<F>::T;
+
+template <class C, class S, class VS, class SO>
+cudaError_t run(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, const int* m_dev,
+                const void* V, int ldV, const int* r_dev, void* Y, int64_t ldy, int* status,
+                cudaStream_t s) {
+  auto k = k_tsmm<C, S, VS, SO>;
+  if (c.smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<(unsigned)c.ctas, 256, c.smem, s>>>(static_cast<const S*>(W), rows, ld, m_dev, c.m_max,
+                                          static_cast<const VS*>(V), ldV, r_dev, c.r_max,
+                                          static_cast<SO*>(Y), ldy, c.tr, c.mstr, c.m_max,
+                                          c.r_max, status);
+  return cudaGetLastError();
+}
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ---------------------------
+__device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                         uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int rnd = 0; rnd < 10; ++rnd) {
+    if (rnd > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+}
+__device__ __forceinline__ double words_to_unit(uint32_t x, uint32_t y) {
+  return ((double)(x >> 5) * 67108864.0 + (double)(y >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+template <class T>
+__global__ void k_gen(T* __restrict__ out, int64_t count, uint64_t seed, int64_t start) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const int64_t b0 = start / 2, b1 = (start + count - 1) / 2;
+  for (int64_t b = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b <= b1;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c0 = (uint32_t)b, c1 = (uint32_t)((uint64_t)b >> 32), c2 = 0, c3 = 0;
+    philox10(c0, c1, c2, c3, k0, k1);
+    const int64_t e0 = 2 * b - start;
+    if (e0 >= 0 && e0 < count) out[e0] = (T)words_to_unit(c0, c1);
+    if (e0 + 1 >= 0 && e0 + 1 < count) out[e0 + 1] = (T)words_to_unit(c2, c3);
+  }
+}
+
+}  // namespace
+
+TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int64_t rows,
+                  int nsm) {
+  TsmmCfg c;
+  c.in = in; c.comp = comp; c.vfmt = vfmt; c.out = out;
+  c.m_max = m_max; c.r_max = r_max;
+  c.mstr = m_max | 1;
+  const size_t es = fmt_bytes(comp);
+  const size_t vbytes = (size_t)m_max * r_max * es;
+  const size_t budget = 200 * 1024;
+  int tr = 128;
+  while (tr > 16 && vbytes + (size_t)tr * c.mstr * es > budget) tr /= 2;
+  c.tr = tr;
+  c.smem = vbytes + (size_t)tr * c.mstr * es;
+  const int64_t ntiles = (rows + tr - 1) / tr;
+  const int per_sm = c.smem > 100 * 1024 ? 1 : (c.smem > 56 * 1024 ? 2 : 4);
+  int64_t ctas = (int64_t)nsm * per_sm;
+  if (ctas > ntiles) ctas = ntiles;
+  if (ctas < 1) ctas = 1;
+  c.ctas = ctas;
+  return c;
+}
+
+cudaError_t launch_tsmm(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
+                        const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
+                        int64_t ldy, int* status, cudaStream_t s) {
+#define TT_TSMM(IN, CO, VF, OUT)                                                                \
+  if (c.in == Fmt::IN && c.comp == Fmt::CO && c.vfmt == Fmt::VF && c.out == Fmt::OUT)           \
+    return run<T_<Fmt::CO>, T_<Fmt::IN>, T_<Fmt::VF>, T_<Fmt::OUT>>(c, W, rows, ld, m_dev, V, ldV, \
+                                                                    r_dev, Y, ldy, status, s);
+  TT_TSMM(F64, DF, DF, DF)
+  TT_TSMM(DF, DF, DF, DF)
+  TT_TSMM(F64, F64, F64, F64)
+  TT_TSMM(F32, F32, DF, F32)
+  TT_TSMM(F64, DF, F64, F64)
+  TT_TSMM(F32, F32, F64, F64)
+#undef TT_TSMM
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gen_uniform(void* out, Fmt f, int64_t count, uint64_t seed, int64_t start,
+                               cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int64_t blocks_needed = ((start + count - 1) / 2 - start / 2 + 1 + 255) / 256;
+  const unsigned g = (unsigned)(blocks_needed < 152 * 16 ? (blocks_needed < 1 ? 1 : blocks_needed) : 152 * 16);
+  if (f == Fmt::F64) k_gen<double><<<g, 256, 0, s>>>((double*)out, count, seed, start);
+  else if (f == Fmt::F32) k_gen<float><<<g, 256, 0, s>>>((float*)out, count, seed, start);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace tt

@@ -1,0 +1,80 @@
+// tsqr.cu -- instantiation and launch of the TSQR level kernels.
+#include "tsqr_kernels.cuh"
+
+namespace tt {
+
+namespace {
+
+template <int MAXM, class C, class S, class RO>
+cudaError_t run_narrow(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout,
+                       int64_t ldR, int* status, cudaStream_t s) {
+  constexpr int K = 64 / MAXM;
+  constexpr int NW = 4;
+  if (L.nw < 1 || L.nw > NW) return cudaErrorInvalidValue;
+  k_tsqr_narrow<MAXM, K, NW, C, S, RO><<<(unsigned)L.ctas, L.nw * 32, 0, s>>>(
+      static_cast<const S*>(W), L.rows, ld, m_dev, L.mval, static_cast<RO*>(Rout), ldR, L.mb,
+      L.panels, status);
+  return cudaGetLastError();
+}
+
+template <int NCH, class C, class S, class RO>
+cudaError_t run_wide(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout,
+                     int64_t ldR, void* Rscr, int* status, cudaStream_t s) {
+  auto kern = k_tsqr_wide<NCH, C, S, RO>;
+  if (L.smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L.smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int mstr = (L.mmax | 1);
+  kern<<<(unsigned)L.ctas, L.nw * 32, L.smem, s>>>(static_cast<const S*>(W), L.rows, ld, m_dev,
+                                                  L.mval, L.pr, mstr, static_cast<C*>(Rscr), L.mmax,
+                                                  static_cast<RO*>(Rout), ldR, L.mb, L.panels,
+                                                  status);
+  return cudaGetLastError();
+}
+
+template <class C, class S, class RO>
+cudaError_t run_typed(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout,
+                      int64_t ldR, void* Rscr, int* status, cudaStream_t s) {
+  if (L.kind == 0) {
+    switch (L.maxm) {
+      case 4: return run_narrow<4, C, S, RO>(L, W, ld, m_dev, Rout, ldR, status, s);
+      case 8: return run_narrow<8, C, S, RO>(L, W, ld, m_dev, Rout, ldR, status, s);
+      case 16: return run_narrow<16, C, S, RO>(L, W, ld, m_dev, Rout, ldR, status, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (L.maxm / 32) {
+    case 1: return run_wide<1, C, S, RO>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+    case 2: return run_wide<2, C, S, RO>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+    case 4: return run_wide<4, C, S, RO>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+    case 8: return run_wide<8, C, S, RO>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+    case 16: return run_wide<16, C, S, RO>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+size_t tsqr_wide_scratch_bytes(const TsqrLevel& L) {
+  if (L.kind != 1) return 0;
+  return (size_t)L.warps * L.mmax * L.mmax * fmt_bytes(L.comp);
+}
+
+cudaError_t launch_tsqr_level(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
+                              void* Rout, int64_t ldR, void* Rscr, int* status, cudaStream_t s) {
+  if (L.in == Fmt::F64 && L.comp == Fmt::DF && L.out == Fmt::DF)
+    return run_typed<df, double, df>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+  if (L.in == Fmt::DF && L.comp == Fmt::DF && L.out == Fmt::DF)
+    return run_typed<df, df, df>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+  if (L.in == Fmt::F64 && L.comp == Fmt::F64 && L.out == Fmt::F64)
+    return run_typed<double, double, double>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+  if (L.in == Fmt::F32 && L.comp == Fmt::F32 && L.out == Fmt::F32)
+    return run_typed<float, float, float>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+  if (L.in == Fmt::F32 && L.comp == Fmt::DF && L.out == Fmt::DF)
+    return run_typed<df, float, df>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace tt

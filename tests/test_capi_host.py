@@ -1,0 +1,92 @@
+"""The C-ABI library loads, exports every symbol include/*.h declares, and its
+host-side sizing and argument checks behave (no GPU needed, no compute calls)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2102_00104_gb300 import build as B
+from paper_2102_00104_gb300 import capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return capi.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:tt_status|const\s+char\s*\*)\s+(tt_\w+)\s*\(", txt, flags=re.M))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 18, names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(capi.EXPORTED)
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert capi.tt_status_str(code)
+    assert capi.tt_status_str(99) == "unknown status"
+
+
+def test_query_rejects_bad_arguments(lib):
+    n = capi.i64_array([4, 4, 4])
+    cb, wb = C.c_size_t(0), C.c_size_t(0)
+    assert lib.tt_query(0, n, 2, 0.0, 0, C.byref(cb), C.byref(wb)) == capi.TT_EINVAL
+    assert lib.tt_query(33, n, 2, 0.0, 0, C.byref(cb), C.byref(wb)) == capi.TT_EINVAL
+    assert lib.tt_query(3, n, 0, 0.0, 0, C.byref(cb), C.byref(wb)) == capi.TT_EINVAL
+    assert lib.tt_query(3, n, 2, -1.0, 0, C.byref(cb), C.byref(wb)) == capi.TT_EINVAL
+    assert lib.tt_query(3, n, 2, 0.0, 7, C.byref(cb), C.byref(wb)) == capi.TT_EINVAL
+    bad = capi.i64_array([4, 0, 4])
+    assert lib.tt_query(3, bad, 2, 0.0, 0, C.byref(cb), C.byref(wb)) == capi.TT_EINVAL
+    assert lib.tt_query(3, n, 2, 0.0, 0, C.byref(cb), C.byref(wb)) == capi.TT_OK
+    assert wb.value > 0 and cb.value == 8 * (1 * 4 * 2 + 2 * 4 * 2 + 2 * 4 * 1)
+
+
+def test_svd_rejects_bad_pointers_before_launch(lib):
+    n = capi.i64_array([4, 4])
+    cores = capi.ptr_array([0, 0])
+    code = lib.tt_svd(None, 0, 2, n, 2, 0.0, cores, None, None, None, None, 0, None)
+    assert code == capi.TT_EINVAL
+    # misaligned workspace is rejected on the host
+    cores = capi.ptr_array([1024, 2048])
+    code = lib.tt_svd(C.c_void_p(4096), 0, 2, n, 2, 0.0, cores, None, None, None, C.c_void_p(4097), 1 << 20, None)
+    assert code == capi.TT_EINVAL
+    # workspace too small
+    code = lib.tt_svd(C.c_void_p(4096), 0, 2, n, 2, 0.0, cores, None, None, None, C.c_void_p(4096), 16, None)
+    assert code == capi.TT_ENOMEM
+
+
+def test_core_caps_are_worst_case_ranks(lib):
+    caps, stride, count = capi.tt_core_caps(10, [8] * 10, 10)
+    # r_k = min(10, 8^k, 8^(10-k)): 8, 10, ..., 10, 8
+    r = [1, 8] + [10] * 7 + [8, 1]
+    assert caps == [r[i] * 8 * r[i + 1] for i in range(10)]
+    assert stride == 80 and count == 80 * 9
+    caps, stride, count = capi.tt_core_caps(1, [7], 3)
+    assert caps == [7] and count == 0
+
+
+def test_block_queries(lib):
+    assert capi.tt_tsqr_query(1000, 8, 0) > 0
+    assert capi.tt_small_svd_query(64) > 0
+    wb = C.c_size_t(0)
+    assert lib.tt_tsqr_query(0, 8, 0, C.byref(wb)) == capi.TT_EINVAL
+    assert lib.tt_tsqr_query(10, 513, 0, C.byref(wb)) == capi.TT_EINVAL
+    assert lib.tt_small_svd_query(0, C.byref(wb)) == capi.TT_EINVAL
+    # unfoldings wider than the engine's limit are refused up front
+    cb = C.c_size_t(0)
+    assert lib.tt_query(3, capi.i64_array([600, 600, 600]), 600, 0.0, 0, C.byref(cb), C.byref(wb)) == capi.TT_ENOTIMPL

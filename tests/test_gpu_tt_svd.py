@@ -1,0 +1,136 @@
+"""End-to-end GPU parity of tt_svd (Alg. 2 on the device) against the Alg. 1 oracle.
+
+Bar (FP64 form): ranks bit-exact; kept singular values of every computed step
+within 1e-10 * sigma_max; relative reconstruction error within 1e-10 of the
+oracle's; discarded energy within 1e-10 ||X||^2; cores 2..d orthonormal.
+FP32 form: the same at 1e-5, against the oracle run on the FP32 values widened
+to FP64 (and the error against the FP64 tensor is reported by the bench).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import tt_svd_oracle as O
+from paper_2102_00104_gb300 import api
+from paper_2102_00104_gb300.inputs import planted_tt, uniform_tensor
+from tests.gpu_common import ensure_lib, fortran_flat
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_lib()
+
+
+def run_gpu(X, r_max, tol=0.0, dtype=torch.float64, arith="df", no_elide=False):
+    dims = X.shape
+    plan = api.TTSVDPlan(dims, r_max, tol, dtype, arith, want_sigma=True, no_elide=no_elide)
+    plan.run(fortran_flat(X, dtype))
+    return plan.result()
+
+
+def compare(X, res, ref, tol_rel):
+    assert res.ranks == ref.ranks, (res.ranks, ref.ranks)
+    smax = max(s[0] for s in ref.sigmas.values())
+    for i, s in ref.sigmas.items():
+        g = res.sigma.get(i)
+        if g is None or torch.isnan(g).any():
+            continue  # elided step: no singular values computed
+        k = ref.ranks[i - 1]
+        got = g.cpu().numpy()[:k]
+        assert np.max(np.abs(got - s[:k])) <= tol_rel * smax, (i, got, s[:k])
+    nx = np.linalg.norm(X)
+    cores = res.core_arrays()
+    err = np.linalg.norm(O.tt_full(cores) - X) / nx
+    err_ref = np.linalg.norm(O.tt_full(ref.cores) - X) / nx
+    assert abs(err - err_ref) <= tol_rel, (err, err_ref)
+    assert abs(res.err2 - ref.err2) <= tol_rel * nx * nx
+    for c in cores[1:]:
+        assert O.core_orthonormality_defect(c) <= max(1e-12, tol_rel * 10)
+    return err
+
+
+CASES = [
+    ((4,) * 10, 8),          # 4^10, r_max = 8 (the small configuration)
+    ((3, 4, 5, 6, 7), 3),
+    ((2,) * 12, 5),
+    ((5, 6, 7), 100),        # every step elided
+    ((9, 7), 4),             # d = 2: a truncated matrix SVD
+    ((1, 4, 1, 5, 1), 2),    # unit extents
+    ((4, 4, 4, 4, 4), 1),    # r_max = 1
+    ((6, 5, 4, 3, 2), 50),   # ranks capped by the rows (wide unfoldings at the left end)
+    ((8, 8, 8, 8, 8), 10),   # 8^5, m = 80 steps (wide TSQR kernel)
+    ((3, 3, 3, 3, 3, 3, 3, 3, 3), 7),
+    ((17, 3, 11), 5),        # odd extents, ragged panels
+]
+
+
+@pytest.mark.parametrize("dims,r_max", CASES)
+def test_fp64_form_parity(dims, r_max):
+    X = uniform_tensor(dims, seed=sum(dims) + r_max)
+    compare(X, run_gpu(X, r_max), O.tt_svd(X, r_max), 1e-10)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_small_config_seeds(seed):
+    X = uniform_tensor((4,) * 10, seed=seed)
+    compare(X, run_gpu(X, 8), O.tt_svd(X, 8), 1e-10)
+
+
+def test_d1_is_a_copy():
+    X = uniform_tensor((7,), seed=3)
+    res = run_gpu(X, 3)
+    assert res.ranks == [1, 1]
+    assert np.array_equal(res.core_arrays()[0].ravel(), X)
+
+
+@pytest.mark.parametrize("dims,r_max", [((4,) * 8, 6), ((8, 8, 8, 8, 8), 10), ((3, 4, 5, 6, 7), 3)])
+def test_native_f64_arith_parity(dims, r_max):
+    X = uniform_tensor(dims, seed=5)
+    compare(X, run_gpu(X, r_max, arith="f64"), O.tt_svd(X, r_max), 1e-10)
+
+
+@pytest.mark.parametrize("dims,r_max", [((4,) * 8, 6), ((8, 8, 8, 8, 8), 10), ((4,) * 10, 8)])
+def test_no_elide_matches(dims, r_max):
+    X = uniform_tensor(dims, seed=6)
+    compare(X, run_gpu(X, r_max, no_elide=True), O.tt_svd(X, r_max), 1e-10)
+
+
+@pytest.mark.parametrize("dims,rank,tol", [((4,) * 8, 3, 1e-4), ((5, 4, 6, 3, 4), 2, 1e-3),
+                                          ((3,) * 8, 4, 1e-2)])
+def test_tolerance_truncation(dims, rank, tol):
+    X = planted_tt(dims, rank, seed=7, noise_rel=1e-6)
+    ref = O.tt_svd(X, r_max=100, tol=tol)
+    res = run_gpu(X, 100, tol)
+    for i, s in ref.sigmas.items():
+        assert not O.rank_is_ambiguous(s, ref.delta, ref.ranks[i - 1])
+    compare(X, res, ref, 1e-10)
+    assert np.linalg.norm(O.tt_full(res.core_arrays()) - X) <= tol * np.linalg.norm(X)
+
+
+def test_planted_rank_fp64():
+    X = planted_tt((8, 8, 8, 8, 8), 4, seed=9, noise_rel=1e-6)
+    compare(X, run_gpu(X, 10), O.tt_svd(X, 10), 1e-10)
+
+
+@pytest.mark.parametrize("dims,r_max", [((4,) * 10, 8), ((8, 8, 8, 8, 8), 10), ((2,) * 14, 32),
+                                        ((6, 5, 4, 3, 2), 50)])
+def test_fp32_form_parity(dims, r_max):
+    X64 = uniform_tensor(dims, seed=8)
+    X32 = X64.astype(np.float32).astype(np.float64)
+    res = run_gpu(X32, r_max, dtype=torch.float32)
+    compare(X32, res, O.tt_svd(X32, r_max), 1e-5)
+
+
+def test_repeated_runs_are_identical():
+    X = uniform_tensor((4,) * 10, seed=2)
+    plan = api.TTSVDPlan(X.shape, 8, 0.0, torch.float64, "df", want_sigma=True)
+    Xd = fortran_flat(X)
+    plan.run(Xd)
+    a = plan.result()
+    plan.run(Xd)
+    b = plan.result()
+    assert a.ranks == b.ranks
+    for ca, cb in zip(a.cores, b.cores):
+        assert torch.equal(ca, cb)
