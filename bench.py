@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""TT-SVD benchmark: input GB/s of a 2^30-entry FP64 tensor (8^10, 8 GiB) on GB300.
+
+One step = one truncated TT-SVD (Alg. 2: TSQR, small SVD, rank choice, core,
+W*V_r for every step) of an i.i.d. uniform[0,1) 8^10 tensor resident in HBM,
+r_max from --rmax (default 10), no tolerance truncation.  The input (8 GiB) is
+larger than L2 (126 MB), so no flush is needed between steps.
+
+value    = N * 8 GiB / (device time per step, CUDA events, max over ranks), GB/s
+e2e      = the same metric when every step also copies X from pinned host
+           memory and reads the cores, ranks and error back
+roofline = the dominant kernel of the step, timed live with CUDA events inside
+           the timed region by the library's profile mode
+Also reported: the r_max sweep {1,5,10,20,50}, the FP32-storage form at r_max=32,
+the oracle's throughput on host cores (cpu_baseline) and SM clocks.
+
+--impl reference times the CPU oracle (Alg. 1, numpy/LAPACK FP64) on the same
+metric with a bounded sample of the workload.
+
+Multi-GPU (torchrun): every rank decomposes its own tensor (independent
+problems, weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+# float-float FMA = 15 FP32 instructions (TwoProd 2, cross terms 2, TwoSum 6,
+# error adds 2, FastTwoSum 3); measured FP32 FMA rate 35.05e12/s (70.1 TFLOP/s)
+DF_FMA_INSTR = 15
+FP32_FMA_RATE_MEASURED = 35.05e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--rmax", type=int, default=10)
+    p.add_argument("--n", type=int, default=8)
+    p.add_argument("--d", type=int, default=10)
+    p.add_argument("--arith", default="df", choices=["df", "f64"])
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-extras", action="store_true", help="skip sweep, FP32 form, e2e, CPU baseline")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---- clocks during the timed region -------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---- CPU oracle throughput ----------------------------------------------------------------
+def cpu_oracle_rate(n: int, r_max: int, seconds: float, seed: int):
+    """Times the oracle (Alg. 1, FP64) on a bounded sample: n^8 tensors, repeated."""
+    import numpy as np  # noqa: F401
+
+    from oracle import tt_svd_oracle as O
+    from paper_2102_00104_gb300.inputs import uniform_tensor
+
+    dims = (n,) * 8
+    X = uniform_tensor(dims, seed=seed)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        O.tt_svd(X, r_max)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or reps >= 50:
+            break
+    cores = len(os.sched_getaffinity(0))
+    gbs = reps * X.nbytes / el / 1e9
+    return gbs, el / reps, cores, f"{reps} x Alg. 1 on a {n}^8 uniform FP64 tensor ({X.nbytes / 2**20:.0f} MiB), r_max={r_max}"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    K, W = max(1, args.steps), max(0, args.warmup)
+    from oracle import tt_svd_oracle as O
+    from paper_2102_00104_gb300.inputs import uniform_tensor
+    dims = (args.n,) * 8
+    X = uniform_tensor(dims, seed=args.seed)
+    for _ in range(min(W, 1)):
+        O.tt_svd(X, args.rmax)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        O.tt_svd(X, args.rmax)
+    el = (time.perf_counter() - t0) / K
+    gbs = X.nbytes / el / 1e9
+    cores = len(os.sched_getaffinity(0))
+    sample = f"Alg. 1 oracle on a {args.n}^8 uniform FP64 tensor ({X.nbytes / 2**20:.0f} MiB) per step, r_max={args.rmax}"
+    line = {"impl": "reference", "metric": "TT-SVD input GB/s (FP64)", "value": gbs, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": el * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{args.n}^{args.d} FP64 uniform[0,1) TT-SVD, r_max={args.rmax}, tol=0 (sampled as {args.n}^8)"},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- the GPU arm ------------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2102_00104_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def lookup_traffic(kernel: str, workload: str):
+    try:
+        t = json.load(open(TRAFFIC_JSON))
+    except Exception:
+        return None
+    e = t.get(f"{kernel}|{workload}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as G
+    from paper_2102_00104_gb300 import api, capi
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        G.build()
+    if world > 1:
+        dist.barrier()
+    capi.lib()
+
+    K, W = max(1, args.steps), max(3, args.warmup)
+    dims = [args.n] * args.d
+    nbar = args.n ** args.d
+    in_bytes = nbar * 8
+    hbm_peak, peak_src = load_peaks()
+    stream = torch.cuda.current_stream()
+
+    X = api.gen_uniform(nbar, args.seed + 1000 * rank, torch.float64)
+    plan = api.TTSVDPlan(dims, args.rmax, 0.0, torch.float64, args.arith)
+    for _ in range(W):
+        plan.run(X)
+    res = plan.result()
+    ranks = res.ranks
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    launches0 = capi.tt_stats()
+    capi.tt_profile(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        plan.run(X)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    prof = capi.tt_profile_read()
+    capi.tt_profile(False)
+    launches = (capi.tt_stats() - launches0) // K
+    ms = e0.elapsed_time(e1) / K
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * in_bytes / (ms / 1e3) / 1e9
+
+    # per-kernel breakdown from the live events (per launch = per step)
+    agg = {}
+    for r in prof:
+        key = (r["kind"], r["step"])
+        a = agg.setdefault(key, {"ms": 0.0, "bytes": r["bytes"], "flops": r["flops"], "n": 0, "info": r["info"]})
+        a["ms"] += r["ms"]
+        a["n"] += 1
+    per_kernel = []
+    for (kind, step), a in agg.items():
+        t = a["ms"] / a["n"]
+        per_kernel.append({"kernel": kind, "step": step, "ms": t, "share": t / ms, "info": a["info"],
+                           "gbs": a["bytes"] / (t / 1e3) / 1e9,
+                           "tflops_fp64eq": a["flops"] / (t / 1e3) / 1e12, "bytes": a["bytes"], "flops": a["flops"]})
+    per_kernel.sort(key=lambda e: -e["ms"])
+    top = per_kernel[0]
+    workload = f"{args.n}^{args.d} f64 r_max={args.rmax} {args.arith}"
+    hbm_frac = top["gbs"] / hbm_peak
+    if args.arith == "df":
+        alu_peak = 2.0 * FP32_FMA_RATE_MEASURED / DF_FMA_INSTR / 1e12   # FP64-equivalent TFLOP/s
+    else:
+        alu_peak = 1.009  # measured native FP64 FMA rate, TFLOP/s
+    alu_frac = top["tflops_fp64eq"] / alu_peak if top["flops"] > 0 else 0.0
+    kname = f"{top['kernel']}@step{top['step']}"
+    traffic = lookup_traffic(top["kernel"], f"{workload} step{top['step']}")
+    if alu_frac > hbm_frac:
+        roof = {"bound": "alu", "kernel": kname, "achieved": top["tflops_fp64eq"], "peak": alu_peak,
+                "unit": "TFLOP/s (FP64-equivalent)", "frac": alu_frac, "traffic": traffic,
+                "peak_source": "measured FP32 FMA rate / 15 FP32 instructions per float-float FMA" if args.arith == "df" else "measured FP64 FMA rate",
+                "hbm_view": {"achieved": top["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
+                             "peak_source": peak_src}}
+    else:
+        roof = {"bound": "hbm", "kernel": kname, "achieved": top["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_frac, "traffic": traffic, "peak_source": peak_src,
+                "alu_view": {"achieved": top["tflops_fp64eq"], "peak": alu_peak, "frac": alu_frac}}
+    two_read_ms = 2 * in_bytes / (hbm_peak * 1e9) * 1e3
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, stream)
+
+    out = {
+        "metric": "TT-SVD input GB/s vs 2-read HBM roofline (FP64 form)",
+        "value": value, "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.arith == "f64" else "f64 storage, float-float (2xFP32) arithmetic",
+        "data": "synthetic: i.i.d. uniform[0,1) from Philox4x32-10, generated on the device",
+        "config": {"workload": f"TT-SVD of a {args.n}^{args.d} FP64 tensor ({in_bytes / 2**30:.0f} GiB), r_max={args.rmax}, tol=0",
+                   "dims": dims, "r_max": args.rmax, "ranks": ranks, "l2_flush": "input 8 GiB > L2, no flush",
+                   "parallelism": f"{world} independent problem(s), one per GPU"},
+        "two_read_roofline": {"ms": two_read_ms, "frac": two_read_ms / ms, "hbm_gbs": hbm_peak, "source": peak_src},
+        "roofline": roof,
+        "per_kernel": per_kernel[:8],
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    out.update(extras)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, stream):
+    out = {}
+    # e2e: host buffers through the public API, copies inside the timed region
+    try:
+        Xh = torch.empty(nbar, dtype=torch.float64, pin_memory=True)
+        Xh.copy_(X)
+        Xd = torch.empty_like(X)
+        caps_bytes = sum(int(c.numel()) * 8 for c in plan.cores_buf)
+        host_cores = [torch.empty(c.numel(), dtype=torch.float64, pin_memory=True) for c in plan.cores_buf]
+        host_ranks = torch.empty(len(dims) + 1, dtype=torch.int64, pin_memory=True)
+        host_err = torch.empty(1, dtype=torch.float64, pin_memory=True)
+        K2 = 3
+        for it in range(K2 + 1):
+            if it == 1:
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            Xd.copy_(Xh, non_blocking=True)
+            plan.run(Xd)
+            for hc, dc in zip(host_cores, plan.cores_buf):
+                hc.copy_(dc, non_blocking=True)
+            host_ranks.copy_(plan.ranks, non_blocking=True)
+            host_err.copy_(plan.err2, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / K2
+        out["e2e"] = {"value": in_bytes / (ms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
+                      "h2d_bytes_per_step": in_bytes,
+                      "d2h_bytes_per_step": caps_bytes + host_ranks.numel() * 8 + 8}
+        del Xh, Xd
+    except Exception as e:  # pinned 8 GiB may be refused on small hosts
+        out["e2e"] = {"value": None, "unit": "GB/s", "error": str(e)[:200]}
+    # r_max sweep (outside the timed region)
+    sweep = {}
+    for r in (1, 5, 10, 20, 50):
+        p = api.TTSVDPlan(dims, r, 0.0, torch.float64, args.arith)
+        p.run(X)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        a.record(stream)
+        for _ in range(reps):
+            p.run(X)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        sweep[str(r)] = {"ms": ms, "gbs": in_bytes / (ms / 1e3) / 1e9,
+                         "two_read_frac": (2 * in_bytes / (hbm_peak * 1e9) * 1e3) / ms}
+        del p
+    out["rmax_sweep_fp64"] = sweep
+    # FP32-storage form, r_max = 32, and its error against the FP64 form
+    X32 = api.gen_uniform(nbar, args.seed, torch.float32)
+    p32 = api.TTSVDPlan(dims, 32, 0.0, torch.float32, "df")
+    p64 = api.TTSVDPlan(dims, 32, 0.0, torch.float64, args.arith)
+    p32.run(X32)
+    r32 = p32.result()
+    p64.run(X)
+    r64 = p64.result()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    a.record(stream)
+    for _ in range(reps):
+        p32.run(X32)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms32 = a.elapsed_time(b) / reps
+    a.record(stream)
+    for _ in range(reps):
+        p64.run(X)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms64 = a.elapsed_time(b) / reps
+    nx = math.sqrt(float((X * X).sum().item()))
+    out["fp32_form"] = {"r_max": 32, "ms": ms32, "gbs_fp32_input": nbar * 4 / (ms32 / 1e3) / 1e9,
+                        "entries_per_s": nbar / (ms32 / 1e3), "fp64_form_ms_same_rmax": ms64,
+                        "speedup_vs_fp64_form": ms64 / ms32,
+                        "rel_err_fp32": math.sqrt(max(r32.err2, 0.0)) / nx,
+                        "rel_err_fp64": math.sqrt(max(r64.err2, 0.0)) / nx,
+                        "rel_err_diff": abs(math.sqrt(max(r32.err2, 0.0)) - math.sqrt(max(r64.err2, 0.0))) / nx}
+    del X32, p32, p64
+    # oracle on the host cores
+    gbs, sec, cores, sample = cpu_oracle_rate(args.n, args.rmax, args.cpu_seconds, args.seed)
+    out["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                           "sample": sample, "seconds_per_sample": sec}
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

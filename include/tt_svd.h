@@ -192,7 +192,28 @@ tt_status tt_serve_submit(tt_server* s, const tt_job* job, uint64_t* ticket);
 tt_status tt_serve_poll(tt_server* s, uint64_t ticket, int wait, tt_job_result* out);
 tt_status tt_serve_destroy(tt_server* s);
 
+/* ---- measurement -----------------------------------------------------------
+ * tt_profile(1) makes every later tt_svd* call record CUDA events around its
+ * kernels (on the call's stream) together with each kernel's algorithmic bytes
+ * and flops; tt_profile(0) stops; both clear earlier records.  tt_profile_read
+ * synchronises the recorded events and returns up to `max` records:
+ * kinds[k] (0 TSQR first level, 1 TSQR upper levels, 2 SVD of R, 3 rank choice
+ * and core, 4 W*V_r), steps[k] (the step index i), ms[k], bytes[k], flops[k],
+ * info[k] (Jacobi sweeps for kind 2 -- valid while the workspace of that call is
+ * untouched -- else -1).  *n receives the number of records available.  Any
+ * output array may be NULL. */
+tt_status tt_profile(int enable);
+tt_status tt_profile_read(int max, int* n, int* kinds, int* steps, double* ms, double* bytes,
+                          double* flops, int* info);
+
+/* Number of kernels this library has launched since it was loaded. */
+tt_status tt_stats(int64_t* launches);
+
 const char* tt_status_str(tt_status s);
+
+/* Text of the last CUDA failure (TT_ECUDA) seen by a tt_* call on the calling
+ * thread: the CUDA error name and message and the failing call.  Empty if none. */
+const char* tt_last_error(void);
 
 #ifdef __cplusplus
 }

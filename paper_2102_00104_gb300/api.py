@@ -133,7 +133,7 @@ def tsqr(W: torch.Tensor, stream=None) -> torch.Tensor:
     wp = (work.data_ptr() + 255) & ~255
     R = torch.empty(m, m, dtype=torch.float64, device=W.device)  # R^T in C order
     capi.tt_tsqr(W.data_ptr(), dt, rows, m, W.stride(0), R.data_ptr(), wp, wb, _stream_ptr(stream))
-    torch.cuda.synchronize()
+    capi.check(capi.tt_last_device_status(wp, _stream_ptr(stream)), "tt_tsqr (device)")
     return R.t()
 
 
@@ -147,7 +147,7 @@ def small_svd(R: torch.Tensor, stream=None):
     sig = torch.empty(m, dtype=torch.float64, device=R.device)
     V = torch.empty(m, m, dtype=torch.float64, device=R.device)
     capi.tt_small_svd(Rc.data_ptr(), m, sig.data_ptr(), V.data_ptr(), wp, wb, _stream_ptr(stream))
-    torch.cuda.synchronize()
+    capi.check(capi.tt_last_device_status(wp, _stream_ptr(stream)), "tt_small_svd (device)")
     return sig, V.t()
 
 

@@ -23,7 +23,8 @@ TT_ARITH_AUTO, TT_ARITH_DF, TT_ARITH_F64 = 0, 1, 2
 EXPORTED = ["tt_query", "tt_core_caps", "tt_svd", "tt_svd_ex", "tt_last_device_status",
             "tt_tsqr_query", "tt_tsqr", "tt_small_svd_query", "tt_small_svd", "tt_tsmm",
             "tt_gen_uniform", "tt_batched_query", "tt_svd_batched", "tt_serve_create",
-            "tt_serve_submit", "tt_serve_poll", "tt_serve_destroy", "tt_status_str"]
+            "tt_serve_submit", "tt_serve_poll", "tt_serve_destroy", "tt_status_str",
+            "tt_profile", "tt_profile_read", "tt_stats", "tt_last_error"]
 
 
 class tt_opts(C.Structure):
@@ -79,6 +80,11 @@ _SIGS = {
     "tt_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.c_void_p]),
     "tt_serve_destroy": (C.c_int, [C.c_void_p]),
     "tt_status_str": (C.c_char_p, [C.c_int]),
+    "tt_profile": (C.c_int, [C.c_int]),
+    "tt_profile_read": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
+    "tt_stats": (C.c_int, [C.c_void_p]),
+    "tt_last_error": (C.c_char_p, []),
 }
 
 
@@ -102,7 +108,10 @@ def lib(path: str | None = None):
 
 def check(code: int, where: str) -> None:
     if code != TT_OK:
-        raise TTError(code, where)
+        detail = ""
+        if code == TT_ECUDA and _lib is not None:
+            detail = " [" + _lib.tt_last_error().decode() + "]"
+        raise TTError(code, where + detail)
 
 
 def i64_array(vals):
@@ -170,3 +179,30 @@ def tt_gen_uniform(out_ptr, dt, count, seed, start=0, stream=0):
 
 def tt_status_str(code):
     return lib().tt_status_str(code).decode()
+
+
+PROFILE_KINDS = {0: "tsqr_first_level", 1: "tsqr_upper_levels", 2: "svd_of_R", 3: "rank_and_core", 4: "tsmm"}
+
+
+def tt_profile(enable: bool):
+    check(lib().tt_profile(1 if enable else 0), "tt_profile")
+
+
+def tt_profile_read(max_records: int = 100000):
+    n = C.c_int(0)
+    kinds = (C.c_int * max_records)()
+    steps = (C.c_int * max_records)()
+    ms = (C.c_double * max_records)()
+    by = (C.c_double * max_records)()
+    fl = (C.c_double * max_records)()
+    info = (C.c_int * max_records)()
+    check(lib().tt_profile_read(max_records, C.byref(n), kinds, steps, ms, by, fl, info), "tt_profile_read")
+    k = min(n.value, max_records)
+    return [dict(kind=PROFILE_KINDS[kinds[j]], step=steps[j], ms=ms[j], bytes=by[j], flops=fl[j],
+                 info=info[j]) for j in range(k)]
+
+
+def tt_stats() -> int:
+    v = C.c_int64(0)
+    check(lib().tt_stats(C.byref(v)), "tt_stats")
+    return v.value

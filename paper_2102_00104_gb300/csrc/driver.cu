@@ -8,7 +8,9 @@
 // and at the end T^(1) = W^(1) (line 13).  Grids are sized for the worst-case
 // rank r_k = min(r_max, n_1..n_k, n_{k+1}..n_d).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -40,6 +42,55 @@ int num_sms() { load_props(); return g_nsm; }
 size_t max_smem_optin() { load_props(); return g_smem_optin; }
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---- measurement: launch counter and optional per-kernel CUDA events -----------------
+static std::atomic<long long> g_launches{0};
+
+namespace prof {
+struct Rec {
+  int kind, step;
+  double bytes, flops;
+  cudaEvent_t a, b;
+  const int* info_dev;  // optional device int read back with the record (Jacobi sweeps)
+};
+static std::mutex mu;
+static bool on = false;
+static std::vector<Rec> recs;
+static std::vector<cudaEvent_t> pool;
+static size_t pool_used = 0;
+
+static cudaEvent_t take() {
+  if (pool_used == pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    pool.push_back(e);
+  }
+  return pool[pool_used++];
+}
+
+// records an event pair around the kernels issued while it is alive
+struct Scope {
+  bool active = false;
+  cudaStream_t s;
+  Rec r;
+  Scope(int kind, int step, double bytes, double flops, cudaStream_t st,
+        const int* info = nullptr) : s(st) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!on) return;
+    r.kind = kind; r.step = step; r.bytes = bytes; r.flops = flops; r.info_dev = info;
+    r.a = take(); r.b = take();
+    if (!r.a || !r.b) return;
+    cudaEventRecord(r.a, s);
+    active = true;
+  }
+  ~Scope() {
+    if (!active) return;
+    cudaEventRecord(r.b, s);
+    std::lock_guard<std::mutex> lk(mu);
+    recs.push_back(r);
+  }
+};
+}  // namespace prof
 
 // ---- TSQR plan --------------------------------------------------------------------
 static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, bool first,
@@ -85,7 +136,11 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
     warps = std::min<int64_t>(L.panels, warps_cap);
     if (ctas_override > 0) warps = std::min<int64_t>(L.panels, ctas_override * (L.kind ? L.nw : 4));
   } else {
-    warps = std::max<int64_t>(1, std::min<int64_t>(warps_cap, (L.panels + 7) / 8));
+    // upper levels: every warp folds at least 8 panels or 8 stacked R blocks, so the
+    // number of partial R's drops by 8x or more per level
+    const int64_t nblocks = (rows + L.mb - 1) / L.mb;
+    const int64_t units = std::min<int64_t>(L.panels, nblocks);
+    warps = std::max<int64_t>(1, std::min<int64_t>(warps_cap, (units + 7) / 8));
   }
   if (warps < 1) warps = 1;
   const int nwmax = L.kind == 0 ? 4 : L.nw;
@@ -101,16 +156,17 @@ static std::vector<TsqrLevel> plan_tsqr(int64_t rows, int m_max, Fmt in, Fmt com
   Fmt cur = in;
   int64_t r = rows;
   bool first = true;
-  for (int guard = 0; guard < 16; ++guard) {
+  for (int guard = 0; guard < 24; ++guard) {
     const Fmt comp = first ? comp1 : comp2;
     const Fmt out = comp;  // partial R's are stored in the arithmetic of their level
     TsqrLevel L = make_level(r, m_max, cur, comp, out, first, nsm, ctas_override);
     lv.push_back(L);
-    if (L.warps == 1) break;
+    if (L.warps == 1) return lv;
     r = L.warps * L.mb;
     cur = out;
     first = false;
   }
+  lv.clear();  // no single R after the level limit: the caller reports TT_ENOTIMPL
   return lv;
 }
 
@@ -215,6 +271,7 @@ static tt_status build_plan(int d, const int64_t* n, int r_max, double tol, tt_d
     P.m_all_max = std::max(P.m_all_max, S.m_max);
     if (!S.elide) {
       S.levels = plan_tsqr(rows, S.m_max, cur, P.comp_tsqr1, P.comp_tsqr2, nsm, ctas_override);
+      if (S.levels.empty()) return TT_ENOTIMPL;
       for (auto& L : S.levels) {
         P.szR = std::max(P.szR, (size_t)L.warps * L.mb * S.m_max * fmt_bytes(L.out));
         P.szRscr = std::max(P.szRscr, tsqr_wide_scratch_bytes(L));
@@ -247,8 +304,19 @@ static tt_status build_plan(int d, const int64_t* n, int r_max, double tol, tt_d
   return TT_OK;
 }
 
-static tt_status cuda_err(cudaError_t e) { return e == cudaSuccess ? TT_OK : TT_ECUDA; }
-#define TT_CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return TT_ECUDA; } while (0)
+// last CUDA failure seen by a tt_* call on this thread (tt_last_error)
+static thread_local char g_last_err[256] = "";
+static void note_err(cudaError_t e, const char* what, int line) {
+  snprintf(g_last_err, sizeof(g_last_err), "%s (%s) at driver.cu:%d: %s", cudaGetErrorName(e),
+           cudaGetErrorString(e), line, what);
+}
+static tt_status cuda_err_at(cudaError_t e, const char* what, int line) {
+  if (e == cudaSuccess) return TT_OK;
+  note_err(e, what, line);
+  return TT_ECUDA;
+}
+#define cuda_err(x) cuda_err_at((x), #x, __LINE__)
+#define TT_CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { note_err(e_, #x, __LINE__); return TT_ECUDA; } } while (0)
 
 static void sigma_layout(int d, const int64_t* n, const int* rw, int64_t* stride, int64_t* count) {
   int64_t s = 1;
@@ -273,6 +341,7 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
   int64_t sig_stride = 0, sig_count = 0;
   sigma_layout(d, P.n, P.r_worst, &sig_stride, &sig_count);
   TT_CK(launch_init_state(st, d, P.n, s));
+  ++g_launches;
   const void* cur = X;
   Fmt cur_fmt = P.xfmt;
   int64_t rows = 1;
@@ -283,9 +352,10 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
     double* sig_step = sigma_out ? sigma_out + (int64_t)(d - i) * sig_stride : nullptr;
     if (S.elide) {
       TT_CK(launch_core_identity(S.m_max, cores_out[i - 1], s));
-      if (sig_step) TT_CK(launch_fill_nan(sig_step, sig_stride, s));
+      if (sig_step) { TT_CK(launch_fill_nan(sig_step, sig_stride, s)); ++g_launches; }
       // record r_{i-1} = m_i and m_{i-1} = n_{i-1} m_i on the device
       TT_CK(launch_set_rank(st, i, (int)P.n[i - 2], S.m_max, s));
+      g_launches += 2;
       rows /= P.n[i - 2];
       continue;
     }
@@ -295,11 +365,17 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
     void* Rfin = nullptr;
     int64_t ldRfin = 0;
     Fmt rfmt = Fmt::DF;
+    const double mm = (double)S.m_max;
     for (size_t l = 0; l < S.levels.size(); ++l) {
       const TsqrLevel& L = S.levels[l];
       void* Rout = wb + P.off_R[l & 1];
       const int64_t ldR = L.warps * L.mb;
-      TT_CK(launch_tsqr_level(L, lin, lld, &st->m[i], Rout, ldR, wb + P.off_Rscr, status, s));
+      {
+        prof::Scope ps(l == 0 ? 0 : 1, i, (double)L.rows * mm * fmt_bytes(L.in),
+                       2.0 * (double)L.rows * mm * mm, s);
+        TT_CK(launch_tsqr_level(L, lin, lld, &st->m[i], Rout, ldR, wb + P.off_Rscr, status, s));
+        ++g_launches;
+      }
       lin = Rout;
       lld = ldR;
       Rfin = Rout;
@@ -309,15 +385,29 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
     // small SVD of R
     double* sig = reinterpret_cast<double*>(wb + P.off_sig);
     void* Vout = wb + P.off_Vout;
-    TT_CK(launch_jacobi(P.comp_svd, rfmt, Rfin, ldRfin, &st->m[i], S.m_max, wb + P.off_A,
-                        wb + P.off_V, P.ldA, sig, Vout, P.ldA, status, s));
+    {
+      prof::Scope ps(2, i, 2.0 * mm * mm * fmt_bytes(P.comp_svd), 0.0, s, &st->sweeps[i]);
+      TT_CK(launch_jacobi(P.comp_svd, rfmt, Rfin, ldRfin, &st->m[i], S.m_max, wb + P.off_A,
+                          wb + P.off_V, P.ldA, sig, Vout, P.ldA, status, &st->sweeps[i], s));
+      ++g_launches;
+    }
     // rank choice, core
-    TT_CK(launch_truncate(sig, rows, i, (int)P.n[i - 2], P.r_max, tol2, st, sig_step, nullptr, s));
-    TT_CK(launch_core(P.comp_svd, Vout, P.ldA, st, i, cores_out[i - 1], s));
+    {
+      prof::Scope ps(3, i, mm * S.r_max_out * 8.0, 0.0, s);
+      TT_CK(launch_truncate(sig, rows, i, (int)P.n[i - 2], P.r_max, tol2, st, sig_step, nullptr, s));
+      TT_CK(launch_core(P.comp_svd, Vout, P.ldA, st, i, cores_out[i - 1], s));
+      g_launches += 2;
+    }
     // W^(i-1) = W^(i) V_r
     void* Y = wb + P.off_W[S.out_buf];
-    TT_CK(launch_tsmm(S.tsmm, cur, rows, rows, &st->m[i], Vout, P.ldA, &st->r[i - 1], Y, rows,
-                      status, s));
+    {
+      const double rr = (double)S.r_max_out;
+      prof::Scope ps(4, i, (double)rows * (mm * fmt_bytes(S.in_fmt) + rr * fmt_bytes(P.inter)),
+                     2.0 * (double)rows * mm * rr, s);
+      TT_CK(launch_tsmm(S.tsmm, cur, rows, rows, &st->m[i], Vout, P.ldA, &st->r[i - 1], Y, rows,
+                        status, s));
+      ++g_launches;
+    }
     cur = Y;
     cur_fmt = P.inter;
     rows /= P.n[i - 2];
@@ -326,6 +416,7 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
   const int64_t cnt = P.n[0] * (int64_t)P.r_worst[1];
   TT_CK(launch_convert_to_f64(cur_fmt, cur, cnt, cores_out[0], s));
   TT_CK(launch_finish(st, d, ranks_out, err2_out, s));
+  g_launches += 2;
   return TT_OK;
 }
 
@@ -349,17 +440,70 @@ const char* tt_status_str(tt_status s) {
   return "unknown status";
 }
 
+const char* tt_last_error(void) { return g_last_err; }
+
+tt_status tt_profile(int enable) {
+  std::lock_guard<std::mutex> lk(prof::mu);
+  prof::on = enable != 0;
+  prof::recs.clear();
+  prof::pool_used = 0;
+  return TT_OK;
+}
+
+tt_status tt_profile_read(int max, int* n, int* kinds, int* steps, double* ms, double* bytes,
+                          double* flops, int* info) {
+  if (max < 0 || !n) return TT_EINVAL;
+  std::lock_guard<std::mutex> lk(prof::mu);
+  *n = (int)prof::recs.size();
+  const int k = std::min<int>(max, (int)prof::recs.size());
+  for (int j = 0; j < k; ++j) {
+    const prof::Rec& r = prof::recs[j];
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return TT_ECUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return TT_ECUDA;
+    if (kinds) kinds[j] = r.kind;
+    if (steps) steps[j] = r.step;
+    if (ms) ms[j] = t;
+    if (bytes) bytes[j] = r.bytes;
+    if (flops) flops[j] = r.flops;
+    if (info) {
+      int v = -1;
+      if (r.info_dev && cudaMemcpy(&v, r.info_dev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TT_ECUDA;
+      info[j] = v;
+    }
+  }
+  return TT_OK;
+}
+
+tt_status tt_stats(int64_t* launches) {
+  if (!launches) return TT_EINVAL;
+  *launches = g_launches.load();
+  return TT_OK;
+}
+
 tt_status tt_query(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
                    size_t* core_bytes, size_t* work_bytes) {
+  // the largest workspace over every tt_opts variant (elision on/off, float-float
+  // or native FP64 arithmetic), so that any options fit a tt_query-sized buffer
   Plan P;
   tt_status st = build_plan(d, n, r_max, tol, dt, nullptr, P);
   if (st != TT_OK) return st;
+  size_t total = P.total;
+  for (int ne = 0; ne <= 1; ++ne)
+    for (int ar = (int)TT_ARITH_DF; ar <= (int)TT_ARITH_F64; ++ar) {
+      tt_opts o{};
+      o.arith = (tt_arith)ar;
+      o.no_elide = ne;
+      Plan Q;
+      if (build_plan(d, n, r_max, tol, dt, &o, Q) == TT_OK) total = std::max(total, Q.total);
+    }
   if (core_bytes) {
     size_t cb = 0;
     for (int i = 1; i <= d; ++i) cb += (size_t)P.r_worst[i - 1] * n[i - 1] * P.r_worst[i] * 8;
     *core_bytes = cb;
   }
-  if (work_bytes) *work_bytes = P.total;
+  if (work_bytes) *work_bytes = total;
   return TT_OK;
 }
 
@@ -419,6 +563,7 @@ tt_status tt_tsqr_query(int64_t rows, int m, tt_dtype dt, size_t* work_bytes) {
   const Fmt in = dt == TT_F32 ? Fmt::F32 : Fmt::F64;
   const Fmt c1 = dt == TT_F32 ? Fmt::F32 : Fmt::DF;
   auto lv = plan_tsqr(rows, m, in, c1, tsqr_comp2(dt), num_sms(), 0);
+  if (lv.empty()) return TT_ENOTIMPL;
   size_t szR = 0, scr = 0;
   for (auto& L : lv) {
     szR = std::max(szR, (size_t)L.warps * L.mb * m * fmt_bytes(L.out));
@@ -489,7 +634,8 @@ tt_status tt_small_svd(const double* R, int m, double* sigma, double* V, void* w
   const size_t szJ = jacobi_scratch_bytes(Fmt::DF, m);
   char* Vw = A + szJ / 2;
   char* Vout = A + align256(szJ);
-  TT_CK(launch_jacobi(Fmt::DF, Fmt::F64, R, m, nullptr, m, A, Vw, mp, sigma, Vout, mp, status, s));
+  TT_CK(launch_jacobi(Fmt::DF, Fmt::F64, R, m, nullptr, m, A, Vw, mp, sigma, Vout, mp, status,
+                      nullptr, s));
   return cuda_err(launch_copy_mat_f64(Fmt::DF, Vout, mp, m, m, 0, V, m, s));
 }
 

@@ -26,6 +26,7 @@ struct DevState {
   double err2;
   int m[40];                   // m[i] = columns of W^(i) (1-based step index)
   int r[40];                   // r[0..d]
+  int sweeps[40];              // Jacobi sweeps used at step i (diagnostics)
 };
 
 constexpr int kMaxM = 512;     // widest unfolding handled
@@ -61,7 +62,7 @@ size_t tsqr_wide_scratch_bytes(const TsqrLevel& L);
 // m_dev may be null: then m = m_max.
 cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
                           int m_max, void* Ag, void* Vg, int ldA, double* sigma, void* Vout,
-                          int ldV, int* status, cudaStream_t s);
+                          int ldV, int* status, int* sweeps_out, cudaStream_t s);
 size_t jacobi_scratch_bytes(Fmt comp, int m_max);
 
 // ---- rank choice / cores --------------------------------------------------------
@@ -89,6 +90,7 @@ struct TsmmCfg {
   Fmt in, comp, vfmt, out;
   int m_max, r_max;
   int tr;           // rows per tile
+  int rc;           // columns of V held in shared memory at a time
   int mstr;         // smem row stride (elements)
   size_t smem;
   int64_t ctas;

@@ -32,16 +32,19 @@ template <class C> __device__ __forceinline__ C from_f32(float x);
 template <> __device__ __forceinline__ df from_f32<df>(float x) { return mkdf(x, 0.f); }
 template <> __device__ __forceinline__ double from_f32<double>(float x) { return (double)x; }
 
-template <class C> __device__ __forceinline__ float conv_tol();
-template <> __device__ __forceinline__ float conv_tol<df>() { return 2e-14f; }
-template <> __device__ __forceinline__ float conv_tol<double>() { return 1e-15f; }
+// Rotation threshold on |cos(a_p, a_q)|: above the rounding floor of an m-term
+// dot product in the working arithmetic (unit roundoff ~2^-46 for the sloppy
+// float-float operations, 2^-53 for FP64), so the sweeps terminate.
+template <class C> __device__ __forceinline__ float conv_tol(int m);
+template <> __device__ __forceinline__ float conv_tol<df>(int m) { return 2.0e-14f * (float)(m < 8 ? 8 : m); }
+template <> __device__ __forceinline__ float conv_tol<double>(int m) { return 2.5e-16f * (float)(m < 8 ? 8 : m); }
 
 // one thread block; A, V in shared memory when `smem_ok`, else in global (Ag, Vg)
 template <class C, class RI>
 __global__ void __launch_bounds__(1024)
 k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, int m_max,
          C* __restrict__ Ag, C* __restrict__ Vg, int ldA, int smem_ok, double* __restrict__ sigma,
-         C* __restrict__ Vout, int ldV, int* status, int max_sweeps) {
+         C* __restrict__ Vout, int ldV, int* status, int* sweeps_out, int max_sweeps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_rot;
   __shared__ int s_exp;
@@ -85,7 +88,26 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
   }
   __syncthreads();
 
-  const float tol = conv_tol<C>();
+  // ||A||_F^2 (FP32 is enough): pairs whose norm product is below tol^2 ||A||_F^2
+  // consist of rounding noise (rank-deficient R) and are not rotated, otherwise
+  // such columns would keep coupling with each other and never converge
+  float fro = 0.f;
+  for (int idx = tid; idx < ldA * mp; idx += nt) {
+    const float v = fp32_hi(A[idx]);
+    fro = fmaf(v, v, fro);
+  }
+  for (int o = 16; o; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+  __syncthreads();
+  if (lane == 0) s_red[wid] = fro;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < nwarps; ++w) t += s_red[w];
+    s_red[0] = t;
+  }
+  __syncthreads();
+  const float tol = conv_tol<C>(m);
+  const float floor_abs = tol * tol * s_red[0];
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) s_rot = 0;
@@ -116,7 +138,7 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
         }
         const float gf = fabsf(fp32_hi(ga));
         const float nf = sqrtf(fp32_hi(al)) * sqrtf(fp32_hi(be));
-        if (gf > tol * nf && gf > 0.f) {
+        if (gf > tol * nf && nf > floor_abs && gf > 0.f) {
           const C zeta = div_(sub(be, al), add(ga, ga));
           const float zf = fp32_hi(zeta);
           const float az = fabsf(zf);
@@ -146,6 +168,7 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
     __syncthreads();
   }
   if (sweep >= max_sweeps && tid == 0 && status) atomicOr(status, DEV_SVD_NOCONV);
+  if (tid == 0 && sweeps_out) *sweeps_out = sweep + 1;
 
   // sigma_k = ||a_k||, sorted descending (stable by index); V columns follow
   C* nrm = smem_ok ? V + (size_t)ldA * mp : reinterpret_cast<C*>(smem_raw);
@@ -287,7 +310,7 @@ __global__ void k_init_state(DevState* st, InitArgs a) {
   st->first_done = 0;
   st->delta2 = 0.0;
   st->err2 = 0.0;
-  for (int i = 0; i < 40; ++i) { st->m[i] = 0; st->r[i] = 1; }
+  for (int i = 0; i < 40; ++i) { st->m[i] = 0; st->r[i] = 1; st->sweeps[i] = 0; }
   st->m[a.d] = a.n[a.d - 1];  // W^(d) has n_d columns (r_d = 1)
 }
 
@@ -317,7 +340,7 @@ size_t jacobi_scratch_bytes(Fmt comp, int m_max) {
 
 cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
                           int m_max, void* Ag, void* Vg, int ldA, double* sigma, void* Vout,
-                          int ldV, int* status, cudaStream_t s) {
+                          int ldV, int* status, int* sweeps_out, cudaStream_t s) {
   const int mp = m_max + (m_max & 1);
   const size_t need = 2ull * ldA * mp * fmt_bytes(comp);
   const int smem_ok = need <= 200 * 1024 ? 1 : 0;
@@ -329,22 +352,22 @@ cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const i
     auto k = k_jacobi<df, df>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<1, threads, smem, s>>>((const df*)R, ldR, m_dev, m_max, (df*)Ag, (df*)Vg, ldA, smem_ok,
-                               sigma, (df*)Vout, ldV, status, sweeps);
+                               sigma, (df*)Vout, ldV, status, sweeps_out, sweeps);
   } else if (comp == Fmt::DF && rin == Fmt::F64) {
     auto k = k_jacobi<df, double>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<1, threads, smem, s>>>((const double*)R, ldR, m_dev, m_max, (df*)Ag, (df*)Vg, ldA,
-                               smem_ok, sigma, (df*)Vout, ldV, status, sweeps);
+                               smem_ok, sigma, (df*)Vout, ldV, status, sweeps_out, sweeps);
   } else if (comp == Fmt::DF && rin == Fmt::F32) {
     auto k = k_jacobi<df, float>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<1, threads, smem, s>>>((const float*)R, ldR, m_dev, m_max, (df*)Ag, (df*)Vg, ldA,
-                               smem_ok, sigma, (df*)Vout, ldV, status, sweeps);
+                               smem_ok, sigma, (df*)Vout, ldV, status, sweeps_out, sweeps);
   } else if (comp == Fmt::F64 && rin == Fmt::F64) {
     auto k = k_jacobi<double, double>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<1, threads, smem, s>>>((const double*)R, ldR, m_dev, m_max, (double*)Ag, (double*)Vg,
-                               ldA, smem_ok, sigma, (double*)Vout, ldV, status, sweeps);
+                               ldA, smem_ok, sigma, (double*)Vout, ldV, status, sweeps_out, sweeps);
   } else {
     return cudaErrorInvalidValue;
   }

@@ -18,21 +18,24 @@ template <class C, class S, class VS, class SO>
 __global__ void __launch_bounds__(256)
 k_tsmm(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
        int m_val, const VS* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
-       SO* __restrict__ Y, int64_t ldy, int tr, int mstr, int m_max, int r_max, int* status) {
+       SO* __restrict__ Y, int64_t ldy, int tr, int mstr, int m_max, int r_max, int rc,
+       int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = m_ptr ? *m_ptr : m_val;
   const int r = r_ptr ? *r_ptr : r_val;
-  if (m < 1 || m > m_max || r < 1 || r > r_max || r > m) {
+  if (m < 1 || m > m_max || r < 1 || r > r_max || r > m || rc < 1) {
     if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
     return;
   }
-  C* Vs = reinterpret_cast<C*>(smem_raw);            // Vs[k * r + c]
-  C* T = Vs + (size_t)m_max * r_max;                 // T[i * mstr + k]
+  C* Vs = reinterpret_cast<C*>(smem_raw);            // chunk of V: Vs[k * rc + (c - c0)]
+  C* T = Vs + (size_t)m_max * rc;                    // tile of W: T[i * mstr + k]
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int idx = tid; idx < m * r; idx += nt) {
-    const int k = idx / r, c = idx % r;
-    Vs[idx] = ld_as<C>(V[k + (size_t)c * ldV]);
-  }
+  const bool v_once = rc >= r;                       // all of V(:, 0:r) fits: load it once
+  if (v_once)
+    for (int idx = tid; idx < m * r; idx += nt) {
+      const int k = idx / r, c = idx % r;
+      Vs[k * rc + c] = ld_as<C>(V[k + (size_t)c * ldV]);
+    }
   const int64_t ntiles = (rows + tr - 1) / tr;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t r0 = t * tr;
@@ -42,14 +45,23 @@ k_tsmm(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict_
       const int64_t row = r0 + i;
       T[(size_t)i * mstr + k] = row < rows ? ld_as<C>(W[row + (int64_t)k * ld]) : Tr<C>::zero();
     }
-    __syncthreads();
-    for (int idx = tid; idx < tr * r; idx += nt) {
-      const int i = idx % tr, c = idx / tr;
-      const int64_t row = r0 + i;
-      const C* ti = T + (size_t)i * mstr;
-      C acc = Tr<C>::zero();
-      for (int k = 0; k < m; ++k) acc = fmac(ti[k], Vs[k * r + c], acc);
-      if (row < rows) Y[row + (int64_t)c * ldy] = st_as<SO>(acc);
+    for (int c0 = 0; c0 < r; c0 += rc) {
+      const int cn = (r - c0) < rc ? (r - c0) : rc;
+      __syncthreads();
+      if (!v_once)
+        for (int idx = tid; idx < m * cn; idx += nt) {
+          const int k = idx / cn, c = idx % cn;
+          Vs[k * rc + c] = ld_as<C>(V[k + (size_t)(c0 + c) * ldV]);
+        }
+      __syncthreads();
+      for (int idx = tid; idx < tr * cn; idx += nt) {
+        const int i = idx % tr, c = idx / tr;
+        const int64_t row = r0 + i;
+        const C* ti = T + (size_t)i * mstr;
+        C acc = Tr<C>::zero();
+        for (int k = 0; k < m; ++k) acc = fmac(ti[k], Vs[k * rc + c], acc);
+        if (row < rows) Y[row + (int64_t)(c0 + c) * ldy] = st_as<SO>(acc);
+      }
     }
   }
 }
@@ -68,7 +80,7 @@ cudaError_t run(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, const
   k<<<(unsigned)c.ctas, 256, c.smem, s>>>(static_cast<const S*>(W), rows, ld, m_dev, c.m_max,
                                           static_cast<const VS*>(V), ldV, r_dev, c.r_max,
                                           static_cast<SO*>(Y), ldy, c.tr, c.mstr, c.m_max,
-                                          c.r_max, status);
+                                          c.r_max, c.rc, status);
   return cudaGetLastError();
 }
 
@@ -117,12 +129,15 @@ TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int
   c.m_max = m_max; c.r_max = r_max;
   c.mstr = m_max | 1;
   const size_t es = fmt_bytes(comp);
-  const size_t vbytes = (size_t)m_max * r_max * es;
   const size_t budget = 200 * 1024;
+  // row tile first (at least 32 rows), then as many V columns as still fit
   int tr = 128;
-  while (tr > 16 && vbytes + (size_t)tr * c.mstr * es > budget) tr /= 2;
+  while (tr > 32 && (size_t)tr * c.mstr * es + (size_t)m_max * es > budget) tr /= 2;
+  int rc = r_max;
+  while (rc > 1 && (size_t)m_max * rc * es + (size_t)tr * c.mstr * es > budget) rc = (rc + 1) / 2;
   c.tr = tr;
-  c.smem = vbytes + (size_t)tr * c.mstr * es;
+  c.rc = rc;
+  c.smem = (size_t)m_max * rc * es + (size_t)tr * c.mstr * es;
   const int64_t ntiles = (rows + tr - 1) / tr;
   const int per_sm = c.smem > 100 * 1024 ? 1 : (c.smem > 56 * 1024 ? 2 : 4);
   int64_t ctas = (int64_t)nsm * per_sm;

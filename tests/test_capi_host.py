@@ -90,3 +90,21 @@ def test_block_queries(lib):
     # unfoldings wider than the engine's limit are refused up front
     cb = C.c_size_t(0)
     assert lib.tt_query(3, capi.i64_array([600, 600, 600]), 600, 0.0, 0, C.byref(cb), C.byref(wb)) == capi.TT_ENOTIMPL
+
+
+def test_tsqr_plans_terminate_for_all_shapes(lib):
+    # every (rows, m) the engine accepts gets a TSQR plan that ends in a single R
+    for m in (1, 2, 5, 8, 13, 16, 17, 31, 33, 64, 100, 160, 200, 256, 320, 400, 512):
+        for rows in (1, 3, 31, 100, 1000, 5000, 65537, 1 << 21, 1 << 27):
+            for dt in (capi.TT_F64, capi.TT_F32):
+                assert capi.tt_tsqr_query(rows, m, dt) > 0, (rows, m, dt)
+
+
+def test_query_paper_configurations(lib):
+    for r in (1, 5, 10, 20, 50):
+        _, wb = capi.tt_query(10, [8] * 10, r, 0.0, capi.TT_F64)
+        assert 0 < wb < 16 << 30
+    _, wb = capi.tt_query(10, [8] * 10, 32, 0.0, capi.TT_F32)
+    assert 0 < wb < 16 << 30
+    _, wb = capi.tt_query(10, [4] * 10, 8, 0.0, capi.TT_F64)
+    assert 0 < wb < 1 << 30

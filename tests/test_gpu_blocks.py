@@ -95,11 +95,12 @@ def test_small_svd(m):
     s_ref = np.linalg.svd(R, compute_uv=False)
     assert np.max(np.abs(sig - s_ref)) <= 1e-12 * s_ref[0]
     assert np.all(np.diff(sig) <= 0)
-    assert np.max(np.abs(V.T @ V - np.eye(m))) <= 1e-12
+    # float-float rotations: orthogonality to ~m * 2^-46
+    assert np.max(np.abs(V.T @ V - np.eye(m))) <= 1e-13 * max(m, 10)
     # R V has orthogonal columns of norms sigma (R = U Sigma V^T)
     RV = R @ V
     G = RV.T @ RV
-    assert np.max(np.abs(G - np.diag(sig ** 2))) <= 1e-12 * s_ref[0] ** 2
+    assert np.max(np.abs(G - np.diag(sig ** 2))) <= 1e-13 * max(m, 10) * s_ref[0] ** 2
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 2e-6)])
@@ -121,3 +122,18 @@ def test_block_argument_errors():
         capi.tt_tsmm(0, 0, 10, 4, 10, 0, 2, 0, 10)
     with pytest.raises(capi.TTError):
         capi.tt_gen_uniform(0, 0, 10, 1)
+
+
+@pytest.mark.parametrize("m,rank", [(80, 8), (42, 5), (64, 1), (9, 0)])
+def test_small_svd_rank_deficient(m, rank):
+    # R of a wide unfolding: only `rank` nonzero rows; the zero singular values
+    # must not stop the sweeps from converging (device status is checked)
+    rng = np.random.default_rng(m + rank)
+    R = np.zeros((m, m))
+    R[:rank] = np.triu(rng.standard_normal((rank, m)))
+    sig, V = api.small_svd(torch.from_numpy(R).cuda())
+    sig, V = sig.cpu().numpy(), V.cpu().numpy()
+    s_ref = np.linalg.svd(R, compute_uv=False)
+    scale = max(s_ref[0], 1.0)
+    assert np.max(np.abs(sig - s_ref)) <= 1e-12 * scale
+    assert np.max(np.abs(V.T @ V - np.eye(m))) <= 1e-13 * max(m, 10)
