@@ -137,6 +137,26 @@ tt_status tt_small_svd_query(int m, size_t* work_bytes);
 tt_status tt_small_svd(const double* R, int m, double* sigma, double* V, void* work,
                        size_t work_bytes, void* stream);
 
+/* tt_small_svd_noalloc: tt_small_svd for callers that cannot allocate device
+ *   memory.  The paper has no counterpart; this is a convenience of the library.
+ *   Who needs it: code that must not call cudaMalloc/cudaFree -- for example a
+ *   component whose device memory belongs to the application's own pool
+ *   allocator, or a loop where an allocation's implicit device synchronisation
+ *   would stall other streams -- and plain-C callers with no workspace at hand.
+ *   It takes the same R, m, sigma and V as tt_small_svd (caller-owned device
+ *   buffers) but no workspace: its scratch (~1.5 MiB) is a static device array
+ *   inside the library, reserved on every GPU that loads the library until the
+ *   process exits.  Limits and rules:
+ *   - m must be in [1, 256]; larger m returns TT_EINVAL (tt_last_error says why).
+ *   - The first call on a device looks up the scratch address for that device
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the one scratch array: calls that can overlap on the GPU
+ *     (different streams without ordering between them) race; order them.
+ *   - A device-side failure (Jacobi sweep limit, non-finite value) is reported
+ *     by sigma[0] = NaN, since there is no workspace status word to read.
+ *   It calls no cudaMalloc, cudaFree or allocating library routine. */
+tt_status tt_small_svd_noalloc(const double* R, int m, double* sigma, double* V, void* stream);
+
 /* tt_tsmm: Y = W V (Sec. 4.1.2 TSMM; with the unpadded layouts used here the
  *   reshape of Alg. 2 line 11 is a view of Y).  W: rows x m (ld), storage dt;
  *   V: device m x k doubles column-major (ldv = m); Y: device rows x k doubles

@@ -24,7 +24,7 @@ EXPORTED = ["tt_query", "tt_core_caps", "tt_svd", "tt_svd_ex", "tt_last_device_s
             "tt_tsqr_query", "tt_tsqr", "tt_small_svd_query", "tt_small_svd", "tt_tsmm",
             "tt_gen_uniform", "tt_batched_query", "tt_svd_batched", "tt_serve_create",
             "tt_serve_submit", "tt_serve_poll", "tt_serve_destroy", "tt_status_str",
-            "tt_profile", "tt_profile_read", "tt_stats", "tt_last_error"]
+            "tt_profile", "tt_profile_read", "tt_stats", "tt_last_error", "tt_small_svd_noalloc"]
 
 
 class tt_opts(C.Structure):
@@ -85,6 +85,7 @@ _SIGS = {
                                   C.c_void_p, C.c_void_p]),
     "tt_stats": (C.c_int, [C.c_void_p]),
     "tt_last_error": (C.c_char_p, []),
+    "tt_small_svd_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -167,6 +168,10 @@ def tt_small_svd_query(m):
 
 def tt_small_svd(R_ptr, m, sigma_ptr, V_ptr, work_ptr, work_bytes, stream=0):
     check(lib().tt_small_svd(R_ptr, m, sigma_ptr, V_ptr, work_ptr, work_bytes, stream), "tt_small_svd")
+
+
+def tt_small_svd_noalloc(R_ptr, m, sigma_ptr, V_ptr, stream=0):
+    check(lib().tt_small_svd_noalloc(R_ptr, m, sigma_ptr, V_ptr, stream), "tt_small_svd_noalloc")
 
 
 def tt_tsmm(W_ptr, dt, rows, m, ld, V_ptr, k, Y_ptr, ldy, stream=0):

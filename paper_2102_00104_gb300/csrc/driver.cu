@@ -316,6 +316,7 @@ static tt_status cuda_err_at(cudaError_t e, const char* what, int line) {
   return TT_ECUDA;
 }
 #define cuda_err(x) cuda_err_at((x), #x, __LINE__)
+void set_last_error_text(const char* text) { snprintf(g_last_err, sizeof(g_last_err), "%s", text); }
 #define TT_CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { note_err(e_, #x, __LINE__); return TT_ECUDA; } } while (0)
 
 static void sigma_layout(int d, const int64_t* n, const int* rw, int64_t* stride, int64_t* count) {

@@ -105,6 +105,9 @@ cudaError_t launch_tsmm(const TsmmCfg& c, const void* W, int64_t rows, int64_t l
 cudaError_t launch_gen_uniform(void* out, Fmt f, int64_t count, uint64_t seed, int64_t start,
                                cudaStream_t s);
 
+// sets the text returned by tt_last_error on the calling thread
+void set_last_error_text(const char* text);
+
 // device properties (cached)
 int num_sms();
 size_t max_smem_optin();

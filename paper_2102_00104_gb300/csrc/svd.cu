@@ -12,7 +12,10 @@
 // c = 1/sqrt(1+t^2), s = c t are then formed in the working arithmetic, so
 // each rotation is orthogonal to working precision even though its angle is
 // only FP32-accurate (the next sweep removes the remaining small coupling).
+#include <mutex>
+
 #include "tsqr_kernels.cuh"
+#include "tt_svd.h"
 
 namespace tt {
 
@@ -442,4 +445,78 @@ cudaError_t launch_finish(const DevState* st, int d, int64_t* ranks_out, double*
   return cudaGetLastError();
 }
 
+// ---- tt_small_svd_noalloc: the Jacobi SVD with its scratch in a static array -----
+//
+// For callers that cannot allocate device memory (see include/tt_svd.h).  The
+// scratch lives in this file-scope device array, so the entry point below
+// calls no cudaMalloc/cudaFree.  Every GPU that loads the library reserves it
+// until the process exits.
+namespace {
+constexpr int kNoAllocMaxM = 256;
+constexpr size_t kNoAllocDf = (size_t)kNoAllocMaxM * kNoAllocMaxM;  // elements of one m x m df matrix
+// layout: [0, 256) status word | A | V (Jacobi working copies) | V result (float-float)
+constexpr size_t kNoAllocBytes = 256 + 3 * kNoAllocDf * sizeof(df);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+static void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+// the device address of g_noalloc_scratch on the current device; looked up once per
+// device (cudaGetSymbolAddress with that device current), then cached
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+// a sweep limit or a non-finite value leaves a nonzero status: report it as sigma[0] = NaN
+__global__ void k_noalloc_mark(const int* status, double* sigma) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && *status != 0)
+    sigma[0] = __longlong_as_double(0x7FF8000000000000ll);
+}
+}  // namespace
+
 }  // namespace tt
+
+extern "C" tt_status tt_small_svd_noalloc(const double* R, int m, double* sigma, double* V,
+                                         void* stream) {
+  using namespace tt;
+  if (!R || !sigma || !V) return TT_EINVAL;
+  if (m < 1 || m > kNoAllocMaxM) {
+    set_last_error_text("tt_small_svd_noalloc: m must be in [1, 256] (size of its static scratch)");
+    return TT_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  void* base = nullptr;
+  cudaError_t e = noalloc_scratch(&base);
+  if (e != cudaSuccess) {
+    set_last_error_text(cudaGetErrorString(e));
+    return TT_ECUDA;
+  }
+  const int mp = m + (m & 1);
+  char* b = static_cast<char*>(base);
+  int* status = reinterpret_cast<int*>(b);
+  df* A = reinterpret_cast<df*>(b + 256);
+  df* Vw = A + kNoAllocDf;
+  df* Vres = Vw + kNoAllocDf;
+  // the status word keeps the previous call's value: clear it; A, V and the result are
+  // written in full by the kernels before they are read
+  if ((e = cudaMemsetAsync(status, 0, sizeof(int), s)) != cudaSuccess) return TT_ECUDA;
+  if ((e = launch_jacobi(Fmt::DF, Fmt::F64, R, m, nullptr, m, A, Vw, mp, sigma, Vres, mp, status,
+                         nullptr, s)) != cudaSuccess)
+    return TT_ECUDA;
+  if ((e = launch_copy_mat_f64(Fmt::DF, Vres, mp, m, m, 0, V, m, s)) != cudaSuccess) return TT_ECUDA;
+  k_noalloc_mark<<<1, 32, 0, s>>>(status, sigma);
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ECUDA;
+}
