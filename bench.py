@@ -199,6 +199,7 @@ def main():
 
     import __graft_entry__ as G
     from paper_2102_00104_gb300 import api, capi
+    from paper_2102_00104_gb300.distributed import max_over_ranks
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -249,10 +250,7 @@ def main():
     capi.tt_profile(False)
     launches = (capi.tt_stats() - launches0) // K
     ms = e0.elapsed_time(e1) / K
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device="cuda")
     value = world * in_bytes / (ms / 1e3) / 1e9
 
     # per-kernel breakdown from the live events (per launch = per step)

@@ -48,8 +48,9 @@ typedef enum {
   TT_ETIMEOUT = 4,   /* a bounded device-side or host-side wait ran out */
   TT_ENOTIMPL = 5,   /* combination not supported */
   TT_ECANCELLED = 6, /* request cancelled (server shut down) */
-  TT_ENUMERIC = 7    /* device-side numerical failure: the Jacobi SVD hit its sweep
+  TT_ENUMERIC = 7,   /* device-side numerical failure: the Jacobi SVD hit its sweep
                         limit or a singular value was not finite */
+  TT_EAGAIN = 8      /* tt_serve_poll: the request has not finished yet */
 } tt_status;
 
 /* Storage precision of the input tensor X.  TT_F64: FP64 tensor.  TT_F32: the
@@ -174,7 +175,12 @@ tt_status tt_gen_uniform(void* out, tt_dtype dt, int64_t count, uint64_t seed, i
                          void* stream);
 
 /* ---- batched form -----------------------------------------------------------
- * Many independent TT-SVDs in one call (same semantics as tt_svd per job). */
+ * Many independent TT-SVDs in one call; each job has the semantics of tt_svd.
+ * The jobs are spread over a pool of library-owned CUDA streams that are forked
+ * from `stream` and joined back into it with events, so the call is
+ * asynchronous on `stream` and can be captured into one CUDA graph.  The
+ * workspace holds one slice per job (tt_batched_query); jobs never share
+ * buffers.  Jobs are started largest first. */
 typedef struct {
   const void* X;            /* device input, Fortran order */
   tt_dtype dtype;
@@ -186,6 +192,7 @@ typedef struct {
   int64_t* ranks_out;       /* device int64[d+1] */
   double* sigma_out;        /* optional */
   double* err2_out;         /* optional */
+  int* status_out;          /* optional device int: the job's device status word */
 } tt_job;
 
 tt_status tt_batched_query(int batch, const tt_job* jobs, size_t* work_bytes);
@@ -193,23 +200,35 @@ tt_status tt_svd_batched(int batch, const tt_job* jobs, void* work, size_t work_
                          void* stream);
 
 /* ---- serve form -------------------------------------------------------------
- * Continuous batching: requests are admitted while others run, as HBM budget
- * and slots free up.  The server owns its workspace (allocated inside
- * hbm_budget_bytes at creation); job inputs and outputs stay caller-owned. */
+ * Continuous batching.  A host scheduler thread admits queued requests (FIFO)
+ * into slots -- one CUDA stream each -- whenever a slot is free and the
+ * request's accounted memory (input + cores + workspace) fits in what is left
+ * of hbm_budget_bytes; requests that arrive while others run start as soon as a
+ * slot and memory free up, and their kernels overlap on the device.  The server
+ * owns one workspace arena (arena_bytes, allocated at creation and
+ * sub-allocated first-fit); inputs and outputs stay caller-owned and must stay
+ * valid until the request is done.  All waits are bounded; nothing spins on the
+ * device. */
 typedef struct tt_server tt_server;
 typedef struct {
-  int max_inflight;         /* concurrent jobs on the device (slots) */
-  int n_streams;            /* CUDA streams used for overlap */
-  double timeout_s;         /* per-request limit for tt_serve_poll (0 = none) */
+  int max_inflight;         /* slots (concurrent requests on the device), >= 1 */
+  size_t arena_bytes;       /* workspace arena; 0 = a quarter of the budget */
+  double timeout_s;         /* limit for a blocking tt_serve_poll (0 = 60 s) */
 } tt_serve_opts;
 typedef struct {
-  tt_status status;
-  double t_submit, t_start, t_done;   /* host clock seconds (steady clock) */
+  tt_status status;         /* TT_OK, a launch error, TT_ENUMERIC, TT_ECANCELLED ... */
+  double t_submit, t_start, t_done;   /* steady-clock seconds: queued, admitted, seen done */
 } tt_job_result;
 
 tt_status tt_serve_create(size_t hbm_budget_bytes, const tt_serve_opts* opts, tt_server** out);
+/* Queue a request (copied); returns TT_ENOMEM if it can never fit the budget or arena. */
 tt_status tt_serve_submit(tt_server* s, const tt_job* job, uint64_t* ticket);
+/* TT_OK with *out filled when the request is done; TT_EAGAIN if not yet (wait = 0);
+ * with wait != 0 blocks up to timeout_s, then TT_ETIMEOUT.  A finished ticket may be
+ * polled again. */
 tt_status tt_serve_poll(tt_server* s, uint64_t ticket, int wait, tt_job_result* out);
+/* Stops admission, cancels queued requests (TT_ECANCELLED), waits (bounded) for
+ * running ones, frees the arena and streams. */
 tt_status tt_serve_destroy(tt_server* s);
 
 /* ---- measurement -----------------------------------------------------------

@@ -161,3 +161,55 @@ def tsmm(W: torch.Tensor, V: torch.Tensor, k: int, stream=None) -> torch.Tensor:
                  rows, _stream_ptr(stream))
     torch.cuda.synchronize()
     return Y
+
+
+class Job:
+    """A tt_job (C struct) with its device output buffers kept alive."""
+
+    def __init__(self, X: torch.Tensor, dims, r_max: int, tol: float = 0.0, want_sigma: bool = False):
+        self.X = X
+        self.dims = [int(x) for x in dims]
+        self.d = len(self.dims)
+        self.r_max = int(r_max)
+        self.tol = float(tol)
+        dev = X.device
+        caps, self.sig_stride, sig_count = capi.tt_core_caps(self.d, self.dims, self.r_max)
+        self.cores_buf = [torch.empty(max(1, c), dtype=torch.float64, device=dev) for c in caps]
+        self.ranks = torch.empty(self.d + 1, dtype=torch.int64, device=dev)
+        self.err2 = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.sigma = torch.empty(max(1, sig_count), dtype=torch.float64, device=dev) if want_sigma else None
+        j = capi.tt_job()
+        j.X = X.data_ptr()
+        j.dtype = _DT[X.dtype]
+        j.d = self.d
+        for i, n in enumerate(self.dims):
+            j.n[i] = n
+        j.r_max = self.r_max
+        j.tol = self.tol
+        for i, t in enumerate(self.cores_buf):
+            j.cores_out[i] = t.data_ptr()
+        j.ranks_out = self.ranks.data_ptr()
+        j.sigma_out = self.sigma.data_ptr() if self.sigma is not None else None
+        j.err2_out = self.err2.data_ptr()
+        j.status_out = self.status.data_ptr()
+        self.c = j
+
+    def result(self) -> TTResult:
+        """Call after the work is complete (stream synchronised / request done)."""
+        r = [int(x) for x in self.ranks.cpu().tolist()]
+        cores = []
+        for i in range(self.d):
+            cnt = r[i] * self.dims[i] * r[i + 1]
+            cores.append(self.cores_buf[i][:cnt].view(r[i + 1], self.dims[i], r[i]).permute(2, 1, 0))
+        return TTResult(cores=cores, ranks=r, err2=float(self.err2.item()))
+
+
+def svd_batched(jobs, stream=None):
+    """Runs tt_svd_batched over Job objects (asynchronous on the stream); returns the workspace."""
+    cj = [j.c for j in jobs]
+    wb = capi.tt_batched_query(cj)
+    work = torch.empty(wb + 256, dtype=torch.uint8, device=jobs[0].X.device)
+    wp = (work.data_ptr() + 255) & ~255
+    capi.tt_svd_batched(cj, wp, wb, _stream_ptr(stream))
+    return work

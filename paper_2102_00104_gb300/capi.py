@@ -14,8 +14,9 @@ LIB_PATH = os.path.join(PKG, "libttsvd.so")
 
 TT_MAX_D = 32
 STATUS = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENOMEM", 3: "TT_ECUDA", 4: "TT_ETIMEOUT",
-          5: "TT_ENOTIMPL", 6: "TT_ECANCELLED", 7: "TT_ENUMERIC"}
-TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_ETIMEOUT, TT_ENOTIMPL, TT_ECANCELLED, TT_ENUMERIC = range(8)
+          5: "TT_ENOTIMPL", 6: "TT_ECANCELLED", 7: "TT_ENUMERIC", 8: "TT_EAGAIN"}
+(TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_ETIMEOUT, TT_ENOTIMPL, TT_ECANCELLED, TT_ENUMERIC,
+ TT_EAGAIN) = range(9)
 TT_F64, TT_F32 = 0, 1
 TT_ARITH_AUTO, TT_ARITH_DF, TT_ARITH_F64 = 0, 1, 2
 
@@ -35,11 +36,11 @@ class tt_job(C.Structure):
     _fields_ = [("X", C.c_void_p), ("dtype", C.c_int), ("d", C.c_int),
                 ("n", C.c_int64 * TT_MAX_D), ("r_max", C.c_int), ("tol", C.c_double),
                 ("cores_out", C.c_void_p * TT_MAX_D), ("ranks_out", C.c_void_p),
-                ("sigma_out", C.c_void_p), ("err2_out", C.c_void_p)]
+                ("sigma_out", C.c_void_p), ("err2_out", C.c_void_p), ("status_out", C.c_void_p)]
 
 
 class tt_serve_opts(C.Structure):
-    _fields_ = [("max_inflight", C.c_int), ("n_streams", C.c_int), ("timeout_s", C.c_double)]
+    _fields_ = [("max_inflight", C.c_int), ("arena_bytes", C.c_size_t), ("timeout_s", C.c_double)]
 
 
 class tt_job_result(C.Structure):
@@ -211,3 +212,40 @@ def tt_stats() -> int:
     v = C.c_int64(0)
     check(lib().tt_stats(C.byref(v)), "tt_stats")
     return v.value
+
+
+# ---- batched and serve forms -------------------------------------------------------------
+def tt_batched_query(jobs) -> int:
+    arr = (tt_job * max(1, len(jobs)))(*jobs)
+    wb = C.c_size_t(0)
+    check(lib().tt_batched_query(len(jobs), arr, C.byref(wb)), "tt_batched_query")
+    return wb.value
+
+
+def tt_svd_batched(jobs, work_ptr, work_bytes, stream=0):
+    arr = (tt_job * max(1, len(jobs)))(*jobs)
+    check(lib().tt_svd_batched(len(jobs), arr, work_ptr, work_bytes, stream), "tt_svd_batched")
+
+
+def tt_serve_create(budget_bytes, max_inflight=8, arena_bytes=0, timeout_s=60.0):
+    srv = C.c_void_p(0)
+    opts = tt_serve_opts(max_inflight, arena_bytes, timeout_s)
+    check(lib().tt_serve_create(budget_bytes, C.byref(opts), C.byref(srv)), "tt_serve_create")
+    return srv
+
+
+def tt_serve_submit(srv, job) -> int:
+    t = C.c_uint64(0)
+    check(lib().tt_serve_submit(srv, C.byref(job), C.byref(t)), "tt_serve_submit")
+    return t.value
+
+
+def tt_serve_poll(srv, ticket, wait=False):
+    """(code, tt_job_result); code is TT_OK when done, TT_EAGAIN while running."""
+    res = tt_job_result()
+    code = lib().tt_serve_poll(srv, ticket, 1 if wait else 0, C.byref(res))
+    return code, res
+
+
+def tt_serve_destroy(srv):
+    check(lib().tt_serve_destroy(srv), "tt_serve_destroy")

@@ -74,6 +74,12 @@ __device__ __forceinline__ df dfdiv(df a, df b) {
   return add(q, mkdf(q3, 0.f));
 }
 __device__ __forceinline__ df div_(df a, df b) { return dfdiv(a, b); }
+// 1/b: FP32 reciprocal and one Newton step in df (relative error ~ (2^-23)^2)
+__device__ __forceinline__ df rcp_(df b) {
+  const float r0 = __frcp_rn(b.hi);
+  const df e = fnmac(b, mkdf(r0, 0.f), mkdf(1.f, 0.f));   // 1 - b r0
+  return fmac(mkdf(r0, 0.f), e, mkdf(r0, 0.f));           // r0 + r0 e
+}
 __device__ __forceinline__ df sqrt_(df a) {
   // one Newton correction of the FP32 root: x + (a - x^2) / (2x), residual in df
   if (!(a.hi > 0.f)) return mkdf(0.f, 0.f);
@@ -103,6 +109,7 @@ __device__ __forceinline__ double mul(double a, double b) { return a * b; }
 __device__ __forceinline__ double fmac(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ double fnmac(double a, double b, double c) { return __fma_rn(-a, b, c); }
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+__device__ __forceinline__ double rcp_(double b) { return 1.0 / b; }
 __device__ __forceinline__ double sqrt_(double a) { return a > 0.0 ? sqrt(a) : 0.0; }
 __device__ __forceinline__ bool is_pos(double a) { return a > 0.0; }
 __device__ __forceinline__ bool is_gt(double a, double b) { return a > b; }
@@ -118,6 +125,7 @@ __device__ __forceinline__ float mul(float a, float b) { return a * b; }
 __device__ __forceinline__ float fmac(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ float fnmac(float a, float b, float c) { return __fmaf_rn(-a, b, c); }
 __device__ __forceinline__ float div_(float a, float b) { return a / b; }
+__device__ __forceinline__ float rcp_(float b) { return 1.0f / b; }
 __device__ __forceinline__ float sqrt_(float a) { return a > 0.f ? sqrtf(a) : 0.f; }
 __device__ __forceinline__ bool is_pos(float a) { return a > 0.f; }
 __device__ __forceinline__ bool is_gt(float a, float b) { return a > b; }

@@ -104,6 +104,31 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
   L.comp = comp;
   L.out = out;
   int64_t warps_cap;
+  int cta_pr = 0, cta_nw = 0, cta_per_sm = 1;
+  const int cta_cfg = m_max > 16 ? tsqr_cta_pick(m_max, comp, &cta_pr, &cta_nw, &cta_per_sm) : -1;
+  if (cta_cfg >= 0) {
+    // CTA-cooperative panels: one partial R per CTA
+    L.kind = 2;
+    L.cfg = cta_cfg;
+    L.maxm = m_max;
+    L.pr = cta_pr;
+    L.nw = cta_nw;
+    L.smem = tsqr_cta_smem(m_max, comp);
+    L.panels = (rows + L.pr - 1) / L.pr;
+    int64_t ctas;
+    if (first) {
+      ctas = std::min<int64_t>(L.panels, (int64_t)nsm * cta_per_sm);
+      if (ctas_override > 0) ctas = std::min<int64_t>(L.panels, ctas_override);
+    } else {
+      // upper levels: enough panels per CTA that a level shrinks the R count >= 4x
+      const int64_t ppc = std::max<int64_t>(2, (4 * (int64_t)L.mb + L.pr - 1) / L.pr);
+      ctas = (L.panels + ppc - 1) / ppc;
+    }
+    if (ctas < 1) ctas = 1;
+    L.ctas = ctas;
+    L.warps = ctas;
+    return L;
+  }
   if (m_max <= 16) {
     L.kind = 0;
     L.maxm = m_max <= 4 ? 4 : (m_max <= 8 ? 8 : 16);

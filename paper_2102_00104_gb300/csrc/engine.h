@@ -37,7 +37,9 @@ constexpr int kMaxM = 512;     // widest unfolding handled
 // (m x m, zero below the diagonal) as a block of `mb` rows of the stacked
 // column-major output (ldR = warps * mb rows).
 struct TsqrLevel {
-  int kind;          // 0 = narrow (register panels), 1 = wide (smem panels)
+  int kind;          // 0 = narrow (warp, register panels), 1 = wide (warp, smem panels),
+                     // 2 = CTA-cooperative (register panels, R in shared memory)
+  int cfg;           // kind 2: layout id (see tsqr_cta.cu)
   int maxm;          // narrow: 4/8/16 ; wide: 32*chunks (template bound)
   int mmax;          // worst-case m of this level (<= maxm)
   int mval;          // m passed by value when the device pointer is null
@@ -55,6 +57,11 @@ struct TsqrLevel {
 cudaError_t launch_tsqr_level(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
                               void* Rout, int64_t ldR, void* Rscr, int* status, cudaStream_t s);
 size_t tsqr_wide_scratch_bytes(const TsqrLevel& L);
+// kind 2: layout id for m_max (or -1 if R does not fit in shared memory), rows per panel, warps
+int tsqr_cta_pick(int m_max, Fmt comp, int* pr, int* nw, int* per_sm);
+size_t tsqr_cta_smem(int m_max, Fmt comp);
+cudaError_t launch_tsqr_cta(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
+                            void* Rout, int64_t ldR, int* status, cudaStream_t s);
 
 // ---- small SVD ------------------------------------------------------------------
 // One-sided Jacobi of the m x m matrix R (format rin, leading dimension ldR);
@@ -87,6 +94,8 @@ cudaError_t launch_finish(const DevState* st, int d, int64_t* ranks_out, double*
 // Y (rows x r, ldy, format out) = W (rows x m, ld, format in) * V(:, 0:r)
 // (V format vfmt, ldV); m = m_dev[0], r = r_dev[0]; comp = arithmetic.
 struct TsmmCfg {
+  int kind;         // 0 = shared-memory tile of W, 1 = register-blocked (V in shared memory)
+  int cpt;          // kind 1: output columns per thread and pass
   Fmt in, comp, vfmt, out;
   int m_max, r_max;
   int tr;           // rows per tile

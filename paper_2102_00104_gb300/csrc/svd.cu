@@ -5,13 +5,14 @@
 // pairs until they are mutually orthogonal; then sigma_j = ||a_j|| and the
 // accumulated rotations form V.  It works on R itself (never on R^T R), so
 // small singular values keep their accuracy.  Pairs follow the round-robin
-// (circle) ordering: m-1 rounds of m/2 disjoint pairs per sweep, one warp per
-// pair.  The rotation angle is taken from zeta = (beta - alpha) / (2 gamma)
+// (circle) ordering: m-1 rounds of m/2 disjoint pairs per sweep, one group of
+// 8-32 lanes per pair.  The rotation angle is taken from zeta = (beta - alpha) / (2 gamma)
 // with t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) (the 2x2 symmetric Schur
-// decomposition of [[alpha, gamma], [gamma, beta]]); t is formed in FP32 and
-// c = 1/sqrt(1+t^2), s = c t are then formed in the working arithmetic, so
-// each rotation is orthogonal to working precision even though its angle is
-// only FP32-accurate (the next sweep removes the remaining small coupling).
+// decomposition of [[alpha, gamma], [gamma, beta]]); beta - alpha is formed in
+// the working arithmetic, zeta and t in FP32, and c = 1/sqrt(1+t^2), s = c t in
+// the working arithmetic, so each rotation is orthogonal to working precision
+// even though its angle is only FP32-accurate (the next sweep removes the
+// remaining small coupling).
 #include <mutex>
 
 #include "tsqr_kernels.cuh"
@@ -42,8 +43,45 @@ template <class C> __device__ __forceinline__ float conv_tol(int m);
 template <> __device__ __forceinline__ float conv_tol<df>(int m) { return 2.0e-14f * (float)(m < 8 ? 8 : m); }
 template <> __device__ __forceinline__ float conv_tol<double>(int m) { return 2.5e-16f * (float)(m < 8 ? 8 : m); }
 
-// one thread block; A, V in shared memory when `smem_ok`, else in global (Ag, Vg)
-template <class C, class RI>
+// float-float (or FP64) rotation parameters from an FP32-accurate tangent t:
+// c = 1 / sqrt(1 + t^2) to working precision (two Newton steps c <- c + c (1 - u c^2) / 2
+// from the FP32 reciprocal square root), s = c t, so c^2 + s^2 = 1 to working precision.
+__device__ __forceinline__ void rot_cs(float t, df& c, df& sn) {
+  float p, e;
+  eft_two_prod(t, t, p, e);
+  const df u = add(mkdf(1.f, 0.f), mkdf(p, e));       // 1 + t^2, exact up to df rounding
+  df cc = mkdf(rsqrtf(u.hi), 0.f);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const df r = fnmac(u, mul(cc, cc), mkdf(1.f, 0.f));  // 1 - u c^2
+    cc = fmac(mul(cc, mkdf(0.5f, 0.f)), r, cc);
+  }
+  c = cc;
+  sn = mul(cc, mkdf(t, 0.f));
+}
+__device__ __forceinline__ void rot_cs(float t, double& c, double& sn) {
+  c = 1.0 / sqrt(1.0 + (double)t * (double)t);
+  sn = c * (double)t;
+}
+
+// masked butterfly inside a group of G lanes (G divides 32, groups are aligned)
+template <int G>
+__device__ __forceinline__ df gsum(df a, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+    a = add(a, mkdf(__shfl_xor_sync(mask, a.hi, o), __shfl_xor_sync(mask, a.lo, o)));
+  return a;
+}
+template <int G>
+__device__ __forceinline__ double gsum(double a, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(mask, a, o);
+  return a;
+}
+
+// One thread block; A, V in shared memory when `smem_ok`, else in global (Ag, Vg).
+// Each pair (p, q) of a round is handled by a group of G lanes.
+template <class C, class RI, int G>
 __global__ void __launch_bounds__(1024)
 k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, int m_max,
          C* __restrict__ Ag, C* __restrict__ Vg, int ldA, int smem_ok, double* __restrict__ sigma,
@@ -111,12 +149,15 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
   __syncthreads();
   const float tol = conv_tol<C>(m);
   const float floor_abs = tol * tol * s_red[0];
+  const int gid = tid / G, gl = tid % G, ngroups = nt / G;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int rnd = 0; rnd < mp - 1; ++rnd) {
-      for (int slot = wid; slot < mp / 2; slot += nwarps) {
+      for (int slot = gid; slot < mp / 2; slot += ngroups) {
         int p, q;
         if (slot == 0) {
           p = mp - 1;
@@ -128,41 +169,38 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
         C* ap = A + (size_t)p * ldA;
         C* aq = A + (size_t)q * ldA;
         C al = Tr<C>::zero(), be = Tr<C>::zero(), ga = Tr<C>::zero();
-        for (int i = lane; i < m; i += 32) {
+        for (int i = gl; i < m; i += G) {
           const C x = ap[i], y = aq[i];
           al = fmac(x, x, al);
           be = fmac(y, y, be);
           ga = fmac(x, y, ga);
         }
-        for (int o = 16; o; o >>= 1) {
-          al = add(al, shfl_xor(al, o));
-          be = add(be, shfl_xor(be, o));
-          ga = add(ga, shfl_xor(ga, o));
-        }
+        al = gsum<G>(al, gmask);
+        be = gsum<G>(be, gmask);
+        ga = gsum<G>(ga, gmask);
         const float gf = fabsf(fp32_hi(ga));
         const float nf = sqrtf(fp32_hi(al)) * sqrtf(fp32_hi(be));
         if (gf > tol * nf && nf > floor_abs && gf > 0.f) {
-          const C zeta = div_(sub(be, al), add(ga, ga));
-          const float zf = fp32_hi(zeta);
+          // zeta = (beta - alpha) / (2 gamma): difference in working precision, quotient in FP32
+          const float zf = fp32_hi(sub(be, al)) / (2.f * fp32_hi(ga));
           const float az = fabsf(zf);
           float tf = az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f)));
           if (zf < 0.f) tf = -tf;
-          const C t = from_f32<C>(tf);
-          const C c = div_(Tr<C>::one(), sqrt_(fmac(t, t, Tr<C>::one())));
-          const C s = mul(c, t);
-          for (int i = lane; i < m; i += 32) {
+          C c, s;
+          rot_cs(tf, c, s);
+          for (int i = gl; i < m; i += G) {
             const C x = ap[i], y = aq[i];
             ap[i] = fnmac(s, y, mul(c, x));
             aq[i] = fmac(s, x, mul(c, y));
           }
           C* vp = V + (size_t)p * ldA;
           C* vq = V + (size_t)q * ldA;
-          for (int i = lane; i < mp; i += 32) {
+          for (int i = gl; i < mp; i += G) {
             const C x = vp[i], y = vq[i];
             vp[i] = fnmac(s, y, mul(c, x));
             vq[i] = fmac(s, x, mul(c, y));
           }
-          if (lane == 0) s_rot = 1;
+          if (gl == 0) s_rot = 1;
         }
       }
       __syncthreads();
@@ -341,6 +379,33 @@ size_t jacobi_scratch_bytes(Fmt comp, int m_max) {
   return 2ull * mp * mp * fmt_bytes(comp);
 }
 
+template <class C, class RI, int G>
+static void run_jacobi_g(const void* R, int64_t ldR, const int* m_dev, int m_max, void* Ag,
+                         void* Vg, int ldA, int smem_ok, size_t smem, double* sigma, void* Vout,
+                         int ldV, int* status, int* sweeps_out, int sweeps, cudaStream_t s) {
+  const int mp = m_max + (m_max & 1);
+  int threads = ((mp / 2) * G + 31) / 32 * 32;
+  if (threads < 64) threads = 64;
+  if (threads > 1024) threads = 1024;
+  auto k = k_jacobi<C, RI, G>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<1, threads, smem, s>>>(static_cast<const RI*>(R), ldR, m_dev, m_max, static_cast<C*>(Ag),
+                             static_cast<C*>(Vg), ldA, smem_ok, sigma, static_cast<C*>(Vout), ldV,
+                             status, sweeps_out, sweeps);
+}
+
+template <class C, class RI>
+static void run_jacobi(const void* R, int64_t ldR, const int* m_dev, int m_max, void* Ag,
+                       void* Vg, int ldA, int smem_ok, size_t smem, double* sigma, void* Vout,
+                       int ldV, int* status, int* sweeps_out, int sweeps, cudaStream_t s) {
+  if (m_max <= 128)
+    run_jacobi_g<C, RI, 8>(R, ldR, m_dev, m_max, Ag, Vg, ldA, smem_ok, smem, sigma, Vout, ldV, status, sweeps_out, sweeps, s);
+  else if (m_max <= 256)
+    run_jacobi_g<C, RI, 16>(R, ldR, m_dev, m_max, Ag, Vg, ldA, smem_ok, smem, sigma, Vout, ldV, status, sweeps_out, sweeps, s);
+  else
+    run_jacobi_g<C, RI, 32>(R, ldR, m_dev, m_max, Ag, Vg, ldA, smem_ok, smem, sigma, Vout, ldV, status, sweeps_out, sweeps, s);
+}
+
 cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
                           int m_max, void* Ag, void* Vg, int ldA, double* sigma, void* Vout,
                           int ldV, int* status, int* sweeps_out, cudaStream_t s) {
@@ -348,32 +413,17 @@ cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const i
   const size_t need = 2ull * ldA * mp * fmt_bytes(comp);
   const int smem_ok = need <= 200 * 1024 ? 1 : 0;
   const size_t smem = (smem_ok ? need : 0) + (size_t)mp * fmt_bytes(comp);
-  int threads = 32 * ((mp / 2 + 0) > 32 ? 32 : (mp / 2 < 1 ? 1 : mp / 2));
-  if (threads < 64) threads = 64;
   const int sweeps = 60;
-  if (comp == Fmt::DF && rin == Fmt::DF) {
-    auto k = k_jacobi<df, df>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<1, threads, smem, s>>>((const df*)R, ldR, m_dev, m_max, (df*)Ag, (df*)Vg, ldA, smem_ok,
-                               sigma, (df*)Vout, ldV, status, sweeps_out, sweeps);
-  } else if (comp == Fmt::DF && rin == Fmt::F64) {
-    auto k = k_jacobi<df, double>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<1, threads, smem, s>>>((const double*)R, ldR, m_dev, m_max, (df*)Ag, (df*)Vg, ldA,
-                               smem_ok, sigma, (df*)Vout, ldV, status, sweeps_out, sweeps);
-  } else if (comp == Fmt::DF && rin == Fmt::F32) {
-    auto k = k_jacobi<df, float>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<1, threads, smem, s>>>((const float*)R, ldR, m_dev, m_max, (df*)Ag, (df*)Vg, ldA,
-                               smem_ok, sigma, (df*)Vout, ldV, status, sweeps_out, sweeps);
-  } else if (comp == Fmt::F64 && rin == Fmt::F64) {
-    auto k = k_jacobi<double, double>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<1, threads, smem, s>>>((const double*)R, ldR, m_dev, m_max, (double*)Ag, (double*)Vg,
-                               ldA, smem_ok, sigma, (double*)Vout, ldV, status, sweeps_out, sweeps);
-  } else {
+  if (comp == Fmt::DF && rin == Fmt::DF)
+    run_jacobi<df, df>(R, ldR, m_dev, m_max, Ag, Vg, ldA, smem_ok, smem, sigma, Vout, ldV, status, sweeps_out, sweeps, s);
+  else if (comp == Fmt::DF && rin == Fmt::F64)
+    run_jacobi<df, double>(R, ldR, m_dev, m_max, Ag, Vg, ldA, smem_ok, smem, sigma, Vout, ldV, status, sweeps_out, sweeps, s);
+  else if (comp == Fmt::DF && rin == Fmt::F32)
+    run_jacobi<df, float>(R, ldR, m_dev, m_max, Ag, Vg, ldA, smem_ok, smem, sigma, Vout, ldV, status, sweeps_out, sweeps, s);
+  else if (comp == Fmt::F64 && rin == Fmt::F64)
+    run_jacobi<double, double>(R, ldR, m_dev, m_max, Ag, Vg, ldA, smem_ok, smem, sigma, Vout, ldV, status, sweeps_out, sweeps, s);
+  else
     return cudaErrorInvalidValue;
-  }
   return cudaGetLastError();
 }
 

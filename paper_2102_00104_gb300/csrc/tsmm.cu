@@ -8,6 +8,8 @@
 // stride) with coalesced loads along the rows, V(:, 0:r) once per CTA, and
 // computes the tr x r outputs with consecutive threads on consecutive rows
 // (coalesced stores).
+#include <algorithm>
+
 #include "tsqr_kernels.cuh"
 
 namespace tt {
@@ -66,12 +68,103 @@ k_tsmm(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict_
   }
 }
 
+// Register-blocked form: V(:, 0:r) sits in shared memory (zero-padded to a multiple of
+// CPT columns); thread t owns rows base + t + 256 q (q < RPT) and CPT output columns at
+// a time, streaming its rows of W from global memory once per column chunk (coalesced
+// across the threads) and accumulating RPT x CPT products in registers.
+template <int RPT, int CPT, class C, class S, class VS, class SO>
+__global__ void __launch_bounds__(256)
+k_tsmm_rb(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
+          int m_val, const VS* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
+          SO* __restrict__ Y, int64_t ldy, int m_max, int r_max, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = m_ptr ? *m_ptr : m_val;
+  const int r = r_ptr ? *r_ptr : r_val;
+  if (m < 1 || m > m_max || r < 1 || r > r_max || r > m) {
+    if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
+    return;
+  }
+  const int rp = (r + CPT - 1) / CPT * CPT;
+  C* Vs = reinterpret_cast<C*>(smem_raw);  // Vs[k * rp + c]
+  for (int idx = threadIdx.x; idx < m * rp; idx += blockDim.x) {
+    const int k = idx / rp, c = idx % rp;
+    Vs[idx] = c < r ? ld_as<C>(V[k + (size_t)c * ldV]) : Tr<C>::zero();
+  }
+  __syncthreads();
+  const int64_t step = (int64_t)gridDim.x * 256 * RPT;
+  for (int64_t base = (int64_t)blockIdx.x * 256 * RPT; base < rows; base += step) {
+    int64_t row[RPT];
+    bool ok[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      row[q] = base + threadIdx.x + 256 * q;
+      ok[q] = row[q] < rows;
+    }
+    for (int c0 = 0; c0 < r; c0 += CPT) {
+      C acc[RPT][CPT];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q)
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) acc[q][cc] = Tr<C>::zero();
+#pragma unroll 4
+      for (int k = 0; k < m; ++k) {
+        C w[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+          w[q] = ok[q] ? ld_as<C>(W[row[q] + (int64_t)k * ld]) : Tr<C>::zero();
+        const C* vk = Vs + k * rp + c0;
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+          const C v = vk[cc];
+#pragma unroll
+          for (int q = 0; q < RPT; ++q) acc[q][cc] = fmac(w[q], v, acc[q][cc]);
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < CPT; ++cc)
+        if (c0 + cc < r)
+#pragma unroll
+          for (int q = 0; q < RPT; ++q)
+            if (ok[q]) Y[row[q] + (int64_t)(c0 + cc) * ldy] = st_as<SO>(acc[q][cc]);
+    }
+  }
+}
+
 template <Fmt F> using T_ = typename FT<F>::T;
+
+template <int RPT, int CPT, class C, class S, class VS, class SO>
+cudaError_t run_rb(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, const int* m_dev,
+                   const void* V, int ldV, const int* r_dev, void* Y, int64_t ldy, int* status,
+                   cudaStream_t s) {
+  auto k = k_tsmm_rb<RPT, CPT, C, S, VS, SO>;
+  if (c.smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<(unsigned)c.ctas, 256, c.smem, s>>>(static_cast<const S*>(W), rows, ld, m_dev, c.m_max,
+                                          static_cast<const VS*>(V), ldV, r_dev, c.r_max,
+                                          static_cast<SO*>(Y), ldy, c.m_max, c.r_max, status);
+  return cudaGetLastError();
+}
 
 template <class C, class S, class VS, class SO>
 cudaError_t run(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, const int* m_dev,
                 const void* V, int ldV, const int* r_dev, void* Y, int64_t ldy, int* status,
                 cudaStream_t s) {
+  if (c.kind == 1) {
+    switch (c.cpt) {
+      case 1: return run_rb<8, 1, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 2: return run_rb<8, 2, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 4: return run_rb<6, 4, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 5: return run_rb<5, 5, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 8: return run_rb<4, 8, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 10: return run_rb<3, 10, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 16: return run_rb<2, 16, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 20: return run_rb<1, 20, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 25: return run_rb<1, 25, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      default: return run_rb<1, 32, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+    }
+  }
   auto k = k_tsmm<C, S, VS, SO>;
   if (c.smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
@@ -130,6 +223,26 @@ TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int
   c.mstr = m_max | 1;
   const size_t es = fmt_bytes(comp);
   const size_t budget = 200 * 1024;
+  // register-blocked form when V(:, 0:r) fits in shared memory
+  // output columns per pass: the smallest instantiated width >= r_max (r_max = 50 runs as 2 x 25)
+  static const int widths[] = {1, 2, 4, 5, 8, 10, 16, 20, 25, 32};
+  c.cpt = 32;
+  for (int w : widths)
+    if (w >= r_max) { c.cpt = w; break; }
+  if (r_max > 32 && r_max <= 50) c.cpt = 25;
+  const int rp = (r_max + c.cpt - 1) / c.cpt * c.cpt;
+  if ((size_t)m_max * rp * es <= budget) {
+    c.kind = 1;
+    c.tr = 0;
+    c.rc = 0;
+    c.smem = (size_t)m_max * rp * es;
+    const int rpt = c.cpt <= 2 ? 8 : (c.cpt == 4 ? 6 : (c.cpt == 5 ? 5 : (c.cpt == 8 ? 4 : (c.cpt == 10 ? 3 : (c.cpt == 16 ? 2 : 1)))));
+    const int64_t blocks = (rows + 256 * rpt - 1) / (256 * rpt);
+    const int per_sm = c.smem > 100 * 1024 ? 1 : (c.smem > 56 * 1024 ? 2 : 4);
+    c.ctas = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)nsm * per_sm));
+    return c;
+  }
+  c.kind = 0;
   // row tile first (at least 32 rows), then as many V columns as still fit
   int tr = 128;
   while (tr > 32 && (size_t)tr * c.mstr * es + (size_t)m_max * es > budget) tr /= 2;

@@ -108,3 +108,27 @@ def test_query_paper_configurations(lib):
     assert 0 < wb < 16 << 30
     _, wb = capi.tt_query(10, [4] * 10, 8, 0.0, capi.TT_F64)
     assert 0 < wb < 1 << 30
+
+
+def test_batched_and_serve_argument_checks(lib):
+    wb = C.c_size_t(0)
+    assert lib.tt_batched_query(-1, None, C.byref(wb)) == capi.TT_EINVAL
+    assert lib.tt_batched_query(0, None, C.byref(wb)) == capi.TT_OK and wb.value == 0
+    bad = capi.tt_job()
+    bad.d = 0
+    assert lib.tt_batched_query(1, C.byref(bad), C.byref(wb)) == capi.TT_EINVAL
+    job = capi.tt_job()
+    job.d = 3
+    for i, n in enumerate((4, 5, 6)):
+        job.n[i] = n
+    job.r_max = 3
+    arr = (capi.tt_job * 2)(job, job)
+    assert lib.tt_batched_query(2, arr, C.byref(wb)) == capi.TT_OK
+    single = capi.tt_query(3, [4, 5, 6], 3, 0.0, capi.TT_F64)[1]
+    assert wb.value >= 2 * single
+    assert lib.tt_svd_batched(1, arr, C.c_void_p(4097), 1 << 30, None) == capi.TT_EINVAL
+    srv = C.c_void_p(0)
+    assert lib.tt_serve_create(0, None, C.byref(srv)) == capi.TT_EINVAL
+    res = capi.tt_job_result()
+    assert lib.tt_serve_poll(None, 1, 0, C.byref(res)) == capi.TT_EINVAL
+    assert lib.tt_serve_destroy(None) == capi.TT_EINVAL
