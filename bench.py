@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-extras", action="store_true", help="skip sweep, FP32 form, e2e, CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--serve-seconds", type=float, default=4.0)
     return p.parse_args()
 
 
@@ -398,11 +399,135 @@ def run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, 
                         "rel_err_fp64": math.sqrt(max(r64.err2, 0.0)) / nx,
                         "rel_err_diff": abs(math.sqrt(max(r32.err2, 0.0)) - math.sqrt(max(r64.err2, 0.0))) / nx}
     del X32, p32, p64
+    out["batched"] = bench_batched(api, capi, torch, stream, args.seed)
+    out["serve"] = bench_serve(api, capi, torch, args.seed, args.serve_seconds)
     # oracle on the host cores
     gbs, sec, cores, sample = cpu_oracle_rate(args.n, args.rmax, args.cpu_seconds, args.seed)
     out["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
                            "sample": sample, "seconds_per_sample": sec}
     return out
+
+
+def draw_shape(rng, lo_log2, hi_log2, d_lo, d_hi):
+    """d ~ U{d_lo..d_hi}, target size 2^U(lo, hi), n_j from {2,3,4,8}: the draw whose
+    log2 size is closest to the target (and inside [lo, hi]) out of 1000 tries."""
+    import numpy as np
+    d = int(rng.integers(d_lo, d_hi + 1))
+    target = rng.uniform(lo_log2, hi_log2)
+    best, best_gap = None, None
+    for _ in range(1000):
+        dims = [int(x) for x in rng.choice([2, 3, 4, 8], size=d)]
+        l2 = float(np.log2(np.prod(dims, dtype=np.float64)))
+        if l2 < lo_log2 or l2 > hi_log2:
+            continue
+        gap = abs(l2 - target)
+        if best is None or gap < best_gap:
+            best, best_gap = dims, gap
+    if best is None:
+        best = [2] * int(lo_log2)
+    return best
+
+
+def bench_batched(api, capi, torch, stream, seed, count=256):
+    """256 tensors (d 6..12, n_j in {2,3,4,8}, 2^12..2^24 entries, FP64/FP32, r_max 4..32)
+    in one tt_svd_batched call captured in a CUDA graph; replays are timed."""
+    import numpy as np
+    rng = np.random.default_rng(seed + 4)
+    jobs, in_bytes = [], 0
+    for t in range(count):
+        dims = draw_shape(rng, 12, 24, 6, 12)
+        dt = torch.float64 if rng.random() < 0.5 else torch.float32
+        nent = int(np.prod(dims))
+        X = api.gen_uniform(nent, seed + 10000 + t, dt)
+        jobs.append(api.Job(X, dims, int(rng.integers(4, 33))))
+        in_bytes += nent * (8 if dt == torch.float64 else 4)
+    api.svd_batched(jobs)  # creates the stream pool, warms up
+    torch.cuda.synchronize()
+    cj = [j.c for j in jobs]
+    wb = capi.tt_batched_query(cj)
+    work = torch.empty(wb + 256, dtype=torch.uint8, device="cuda")
+    wp = (work.data_ptr() + 255) & ~255
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            capi.tt_svd_batched(cj, wp, wb, int(s.cuda_stream))
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    reps = 5
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream()
+    a.record(cur)
+    for _ in range(reps):
+        g.replay()
+    b.record(cur)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    bad = sum(int(j.status.item()) != 0 for j in jobs)
+    return {"jobs": count, "ms": ms, "gbs": in_bytes / (ms / 1e3) / 1e9, "input_bytes": in_bytes,
+            "graph": "one CUDA graph replay per batch", "jobs_with_device_errors": bad}
+
+
+def bench_serve(api, capi, torch, seed, seconds):
+    """Poisson arrivals (200 req/s) for a bounded time.  Requests: d 6..14, n_j from
+    {2,3,4,8}, 50/50 FP64/FP32; half use r_max in {4,8,16,32} on uniform inputs of
+    2^14..2^24 entries, half use tol in {1e-2,1e-4} (r_max cap 32) on planted-rank
+    inputs (ranks 4..32, 1e-3 relative noise) of 2^14..2^22 entries.  Inputs come from
+    a pool of device-resident tensors made before the arrivals (not timed)."""
+    import numpy as np
+    from paper_2102_00104_gb300.inputs import planted_tt
+    rng = np.random.default_rng(seed + 5)
+    pool = []
+    for t in range(48):
+        dt = torch.float64 if t % 2 == 0 else torch.float32
+        if t % 4 < 2:
+            dims = draw_shape(rng, 14, 24, 6, 14)
+            X = api.gen_uniform(int(np.prod(dims)), seed + 20000 + t, dt)
+            spec = (int(rng.choice([4, 8, 16, 32])), 0.0)
+        else:
+            dims = draw_shape(rng, 14, 22, 6, 14)
+            Xh = planted_tt(dims, int(rng.integers(4, 33)), seed=t, noise_rel=1e-3)
+            X = torch.from_numpy(Xh.ravel(order="F").copy()).to("cuda", dt)
+            spec = (32, float(rng.choice([1e-2, 1e-4])))
+        pool.append((dims, X, spec))
+    torch.cuda.synchronize()
+    srv = capi.tt_serve_create(150 << 30, max_inflight=16, arena_bytes=48 << 30)
+    n_req = int(200 * seconds)
+    gaps = rng.exponential(1.0 / 200.0, size=n_req)
+    picks = rng.integers(0, len(pool), size=n_req)
+    tickets, jobs, nbytes = [], [], 0
+    t0 = time.perf_counter()
+    due = t0
+    for gap, pk in zip(gaps, picks):
+        due += gap
+        while time.perf_counter() < due:
+            time.sleep(min(1e-4, max(0.0, due - time.perf_counter())))
+        dims, X, (r, tol) = pool[int(pk)]
+        j = api.Job(X, dims, r, tol)
+        jobs.append(j)
+        tickets.append(capi.tt_serve_submit(srv, j.c))
+        nbytes += X.numel() * X.element_size()
+    lat, bad = [], 0
+    first_submit, last_done = None, None
+    for t in tickets:
+        code, res = capi.tt_serve_poll(srv, t, wait=True)
+        if code != capi.TT_OK or res.status != capi.TT_OK:
+            bad += 1
+            continue
+        lat.append(res.t_done - res.t_submit)
+        first_submit = res.t_submit if first_submit is None else min(first_submit, res.t_submit)
+        last_done = res.t_done if last_done is None else max(last_done, res.t_done)
+    capi.tt_serve_destroy(srv)
+    lat.sort()
+    p50 = lat[len(lat) // 2] * 1e3 if lat else None
+    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3 if lat else None
+    span = (last_done - first_submit) if lat else None
+    return {"requests": n_req, "seconds_of_arrivals": seconds, "rate_per_s": 200,
+            "p50_ms": p50, "p99_ms": p99, "failed": bad, "input_bytes": nbytes,
+            "gbs": nbytes / span / 1e9 if span else None,
+            "sizes": "r_max jobs 2^14..2^24 entries, tol jobs 2^14..2^22 (r_max cap 32), d 6..14, pool of 48 device-resident inputs",
+            "budget_bytes": 150 << 30, "slots": 16}
 
 
 if __name__ == "__main__":

@@ -248,6 +248,14 @@ tt_status tt_profile_read(int max, int* n, int* kinds, int* steps, double* ms, d
 /* Number of kernels this library has launched since it was loaded. */
 tt_status tt_stats(int64_t* launches);
 
+/* Tuning parameters, process-wide (used by the autotuner, paper_2102_00104_gb300/
+ * autotune.py).  Keys: "tsqr.cfg.<b>" selects the CTA-cooperative TSQR layout (rows
+ * per panel, lanes per column group) for the m-bucket b = 1 (m <= 64), 2 (m <= 80) or
+ * 3 (m <= 128) among the alternative layouts 16..20; a layout that cannot hold m is
+ * ignored.  value < 0 removes the key.  Results never depend on these settings beyond
+ * rounding. */
+tt_status tt_tune_set(const char* key, int value);
+
 const char* tt_status_str(tt_status s);
 
 /* Text of the last CUDA failure (TT_ECUDA) seen by a tt_* call on the calling

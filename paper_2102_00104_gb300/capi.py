@@ -25,7 +25,7 @@ EXPORTED = ["tt_query", "tt_core_caps", "tt_svd", "tt_svd_ex", "tt_last_device_s
             "tt_tsqr_query", "tt_tsqr", "tt_small_svd_query", "tt_small_svd", "tt_tsmm",
             "tt_gen_uniform", "tt_batched_query", "tt_svd_batched", "tt_serve_create",
             "tt_serve_submit", "tt_serve_poll", "tt_serve_destroy", "tt_status_str",
-            "tt_profile", "tt_profile_read", "tt_stats", "tt_last_error", "tt_small_svd_noalloc"]
+            "tt_profile", "tt_profile_read", "tt_stats", "tt_last_error", "tt_small_svd_noalloc", "tt_tune_set"]
 
 
 class tt_opts(C.Structure):
@@ -87,6 +87,7 @@ _SIGS = {
     "tt_stats": (C.c_int, [C.c_void_p]),
     "tt_last_error": (C.c_char_p, []),
     "tt_small_svd_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tt_tune_set": (C.c_int, [C.c_char_p, C.c_int]),
 }
 
 
@@ -105,6 +106,9 @@ def lib(path: str | None = None):
         f.restype = res
         f.argtypes = args
     _lib = L
+    # layouts chosen by the autotuner on this kind of GPU (tune_table.json), if present
+    from . import autotune
+    autotune.load()
     return L
 
 
@@ -249,3 +253,7 @@ def tt_serve_poll(srv, ticket, wait=False):
 
 def tt_serve_destroy(srv):
     check(lib().tt_serve_destroy(srv), "tt_serve_destroy")
+
+
+def tt_tune_set(key: str, value: int):
+    check(lib().tt_tune_set(key.encode(), int(value)), "tt_tune_set")

@@ -9,6 +9,8 @@
 // rank r_k = min(r_max, n_1..n_k, n_{k+1}..n_d).
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <string>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -42,6 +44,16 @@ int num_sms() { load_props(); return g_nsm; }
 size_t max_smem_optin() { load_props(); return g_smem_optin; }
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---- tuning parameters (set by the autotuner through tt_tune_set) ---------------------
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;
+
+int tune_get(const char* key, int dflt) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  return it == g_tune.end() ? dflt : it->second;
+}
 
 // ---- measurement: launch counter and optional per-kernel CUDA events -----------------
 static std::atomic<long long> g_launches{0};
@@ -113,11 +125,14 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
     L.maxm = m_max;
     L.pr = cta_pr;
     L.nw = cta_nw;
-    L.smem = tsqr_cta_smem(m_max, comp);
+    L.smem = tsqr_cta_smem(m_max, comp, cta_cfg);
     L.panels = (rows + L.pr - 1) / L.pr;
     int64_t ctas;
     if (first) {
-      ctas = std::min<int64_t>(L.panels, (int64_t)nsm * cta_per_sm);
+      // the tree over the partial R's costs ~P m^3 against rows m^2 for this level:
+      // keep P <= rows / (4 m) so the tree stays a fraction of the work
+      const int64_t p_cap = std::max<int64_t>(1, rows / (4 * (int64_t)m_max));
+      ctas = std::min<int64_t>(std::min<int64_t>(L.panels, (int64_t)nsm * cta_per_sm), p_cap);
       if (ctas_override > 0) ctas = std::min<int64_t>(L.panels, ctas_override);
     } else {
       // upper levels: enough panels per CTA that a level shrinks the R count >= 4x
@@ -467,6 +482,14 @@ const char* tt_status_str(tt_status s) {
 }
 
 const char* tt_last_error(void) { return g_last_err; }
+
+tt_status tt_tune_set(const char* key, int value) {
+  if (!key || !*key) return TT_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (value < 0) g_tune.erase(key);
+  else g_tune[key] = value;
+  return TT_OK;
+}
 
 tt_status tt_profile(int enable) {
   std::lock_guard<std::mutex> lk(prof::mu);

@@ -59,9 +59,11 @@ cudaError_t launch_tsqr_level(const TsqrLevel& L, const void* W, int64_t ld, con
 size_t tsqr_wide_scratch_bytes(const TsqrLevel& L);
 // kind 2: layout id for m_max (or -1 if R does not fit in shared memory), rows per panel, warps
 int tsqr_cta_pick(int m_max, Fmt comp, int* pr, int* nw, int* per_sm);
-size_t tsqr_cta_smem(int m_max, Fmt comp);
+size_t tsqr_cta_smem(int m_max, Fmt comp, int id);
+// global-memory R scratch needed by layout `id` for `ctas` CTAs (0 if R sits in shared memory)
+size_t tsqr_cta_scratch(int m_max, Fmt comp, int id, int64_t ctas);
 cudaError_t launch_tsqr_cta(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
-                            void* Rout, int64_t ldR, int* status, cudaStream_t s);
+                            void* Rout, int64_t ldR, void* Rscr, int* status, cudaStream_t s);
 
 // ---- small SVD ------------------------------------------------------------------
 // One-sided Jacobi of the m x m matrix R (format rin, leading dimension ldR);
@@ -71,6 +73,12 @@ cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const i
                           int m_max, void* Ag, void* Vg, int ldA, double* sigma, void* Vout,
                           int ldV, int* status, int* sweeps_out, cudaStream_t s);
 size_t jacobi_scratch_bytes(Fmt comp, int m_max);
+// cluster form (svd_cluster.cu): cluster size for m (0 = single CTA) and its launch
+int jacobi_cluster_plan(Fmt comp, int m_max, int* npl_out);
+int jacobi_cluster_npl(Fmt comp, int m_max, int nc);
+cudaError_t launch_jacobi_cluster(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
+                                  int m_max, int nc, int npl, double* sigma, void* Vout, int ldV,
+                                  int* status, int* sweeps_out, cudaStream_t s);
 
 // ---- rank choice / cores --------------------------------------------------------
 cudaError_t launch_truncate(const double* sigma, int64_t rows, int step_i, int n_next,
@@ -113,6 +121,9 @@ cudaError_t launch_tsmm(const TsmmCfg& c, const void* W, int64_t rows, int64_t l
 // ---- generator -------------------------------------------------------------------
 cudaError_t launch_gen_uniform(void* out, Fmt f, int64_t count, uint64_t seed, int64_t start,
                                cudaStream_t s);
+
+// tuning parameter set through tt_tune_set (dflt if unset)
+int tune_get(const char* key, int dflt);
 
 // sets the text returned by tt_last_error on the calling thread
 void set_last_error_text(const char* text);

@@ -409,6 +409,19 @@ static void run_jacobi(const void* R, int64_t ldR, const int* m_dev, int m_max, 
 cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
                           int m_max, void* Ag, void* Vg, int ldA, double* sigma, void* Vout,
                           int ldV, int* status, int* sweeps_out, cudaStream_t s) {
+  // m > 48: spread the columns over a thread-block cluster when one fits
+  int npl = 0;
+  const int nc = jacobi_cluster_plan(comp, m_max, &npl);
+  if (nc > 0) {
+    for (int cand : {nc, nc == 16 ? 8 : 16}) {
+      const int np = cand == nc ? npl : jacobi_cluster_npl(comp, m_max, cand);
+      if (!np) continue;
+      const cudaError_t e = launch_jacobi_cluster(comp, rin, R, ldR, m_dev, m_max, cand, np, sigma,
+                                                  Vout, ldV, status, sweeps_out, s);
+      if (e == cudaSuccess) return e;
+      cudaGetLastError();  // launch refused (no resident cluster of that size)
+    }
+  }
   const int mp = m_max + (m_max & 1);
   const size_t need = 2ull * ldA * mp * fmt_bytes(comp);
   const int smem_ok = need <= 200 * 1024 ? 1 : 0;

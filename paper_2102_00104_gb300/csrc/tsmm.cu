@@ -72,8 +72,8 @@ k_tsmm(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict_
 // CPT columns); thread t owns rows base + t + 256 q (q < RPT) and CPT output columns at
 // a time, streaming its rows of W from global memory once per column chunk (coalesced
 // across the threads) and accumulating RPT x CPT products in registers.
-template <int RPT, int CPT, class C, class S, class VS, class SO>
-__global__ void __launch_bounds__(256)
+template <int RPT, int CPT, int MINB, class C, class S, class VS, class SO>
+__global__ void __launch_bounds__(256, MINB)
 k_tsmm_rb(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
           int m_val, const VS* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
           SO* __restrict__ Y, int64_t ldy, int m_max, int r_max, int* status) {
@@ -106,7 +106,7 @@ k_tsmm_rb(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
       for (int q = 0; q < RPT; ++q)
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) acc[q][cc] = Tr<C>::zero();
-#pragma unroll 4
+#pragma unroll 8
       for (int k = 0; k < m; ++k) {
         C w[RPT];
 #pragma unroll
@@ -132,11 +132,11 @@ k_tsmm_rb(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
 
 template <Fmt F> using T_ = typename FT<F>::T;
 
-template <int RPT, int CPT, class C, class S, class VS, class SO>
+template <int RPT, int CPT, int MINB, class C, class S, class VS, class SO>
 cudaError_t run_rb(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, const int* m_dev,
                    const void* V, int ldV, const int* r_dev, void* Y, int64_t ldy, int* status,
                    cudaStream_t s) {
-  auto k = k_tsmm_rb<RPT, CPT, C, S, VS, SO>;
+  auto k = k_tsmm_rb<RPT, CPT, MINB, C, S, VS, SO>;
   if (c.smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (e != cudaSuccess) return e;
@@ -152,17 +152,18 @@ cudaError_t run(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, const
                 const void* V, int ldV, const int* r_dev, void* Y, int64_t ldy, int* status,
                 cudaStream_t s) {
   if (c.kind == 1) {
+    // one row per thread and several CTAs per SM keep many loads in flight
     switch (c.cpt) {
-      case 1: return run_rb<8, 1, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-      case 2: return run_rb<8, 2, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-      case 4: return run_rb<6, 4, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-      case 5: return run_rb<5, 5, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-      case 8: return run_rb<4, 8, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-      case 10: return run_rb<3, 10, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-      case 16: return run_rb<2, 16, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-      case 20: return run_rb<1, 20, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-      case 25: return run_rb<1, 25, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-      default: return run_rb<1, 32, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 1: return run_rb<1, 1, 4, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 2: return run_rb<1, 2, 4, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 4: return run_rb<1, 4, 4, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 5: return run_rb<1, 5, 4, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 8: return run_rb<1, 8, 4, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 10: return run_rb<1, 10, 4, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 16: return run_rb<1, 16, 2, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 20: return run_rb<1, 20, 2, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      case 25: return run_rb<1, 25, 2, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+      default: return run_rb<1, 32, 2, C, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
     }
   }
   auto k = k_tsmm<C, S, VS, SO>;
@@ -236,9 +237,8 @@ TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int
     c.tr = 0;
     c.rc = 0;
     c.smem = (size_t)m_max * rp * es;
-    const int rpt = c.cpt <= 2 ? 8 : (c.cpt == 4 ? 6 : (c.cpt == 5 ? 5 : (c.cpt == 8 ? 4 : (c.cpt == 10 ? 3 : (c.cpt == 16 ? 2 : 1)))));
-    const int64_t blocks = (rows + 256 * rpt - 1) / (256 * rpt);
-    const int per_sm = c.smem > 100 * 1024 ? 1 : (c.smem > 56 * 1024 ? 2 : 4);
+    const int64_t blocks = (rows + 255) / 256;
+    const int per_sm = std::min(c.cpt <= 10 ? 4 : 2, c.smem > 100 * 1024 ? 1 : (c.smem > 56 * 1024 ? 2 : 4));
     c.ctas = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)nsm * per_sm));
     return c;
   }

@@ -18,8 +18,8 @@
 // column k ("D-thread", k mod blockDim) sums the warp partials, forms the
 // branch-free reflector of Alg. 6 lines 4-7 from D_j = M_j . M_j and R_jj, and
 // the coefficient c_k = (piv R_jk + M_j . M_k) / t, and updates R_jk; R is kept
-// packed (upper triangle, row-major) in shared memory.  Two __syncthreads per
-// column.
+// packed (upper triangle, row-major) in shared memory (or, for m too large for
+// it, in an L2-resident global slice per CTA).  Two __syncthreads per column.
 #pragma once
 #include "tsqr_kernels.cuh"
 
@@ -28,11 +28,11 @@ namespace tt {
 // packed upper triangle, row-major: row j starts at j*m - j*(j-1)/2 (holds columns j..m-1)
 __device__ __forceinline__ int packed_row(int j, int m) { return j * m - (j * (j - 1)) / 2; }
 
-template <int CG, int CL, int RL, int NW, int MINB, class C, class S, class RO>
+template <int CG, int CL, int RL, int NW, int MINB, bool RG_MEM, class C, class S, class RO>
 __global__ void __launch_bounds__(NW * 32, MINB)
 k_tsqr_cta(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
            int m_val, int mmax, RO* __restrict__ Rout, int64_t ldR, int mb, int64_t npanels,
-           int* status) {
+           C* __restrict__ Rglob, int* status) {
   constexpr int RGW = 32 / CG;
   constexpr int RG = NW * RGW;
   constexpr int PR = RG * RL;
@@ -42,8 +42,11 @@ k_tsqr_cta(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restr
     if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
     return;
   }
-  C* R = reinterpret_cast<C*>(smem_raw);                  // packed triangle of m_max
-  C* red = R + (size_t)mmax * (mmax + 1) / 2;             // red[w * mmax + k]
+  // packed triangle of m_max: in shared memory, or (RG_MEM, large m) in a per-CTA
+  // slice of global memory that stays resident in L2
+  C* R = RG_MEM ? Rglob + (size_t)blockIdx.x * ((size_t)mmax * (mmax + 1) / 2)
+                : reinterpret_cast<C*>(smem_raw);
+  C* red = RG_MEM ? reinterpret_cast<C*>(smem_raw) : R + (size_t)mmax * (mmax + 1) / 2;
   C* Cc = red + (size_t)NW * mmax;                        // coefficients c_k
   const int tid = threadIdx.x, nt = NW * 32;
   const int w = tid >> 5, lane = tid & 31;
