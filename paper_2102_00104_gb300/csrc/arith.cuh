@@ -135,6 +135,35 @@ __device__ __forceinline__ float shfl_xor(float a, int m) { return __shfl_xor_sy
 __device__ __forceinline__ float shfl_idx(float a, int s) { return __shfl_sync(0xffffffffu, a, s); }
 
 // ----------------------------------------------------------------------------
+// lazy float-float sums for reductions: value = s + e with e unnormalised.
+// Each addition is one TwoSum of the leading words plus plain adds of the
+// trailing ones, so a chain of additions waits only on the FP32 add of the
+// leading words; lz_fin normalises once (with a full TwoSum) at the end.
+struct dfl {
+  float s, e;
+};
+__device__ __forceinline__ dfl lz(df a) { dfl r; r.s = a.hi; r.e = a.lo; return r; }
+__device__ __forceinline__ float lz(float a) { return a; }
+__device__ __forceinline__ double lz(double a) { return a; }
+__device__ __forceinline__ dfl lz_add(dfl a, dfl b) {
+  dfl r; float t;
+  eft_two_sum(a.s, b.s, r.s, t);
+  r.e = __fadd_rn(__fadd_rn(a.e, b.e), t);
+  return r;
+}
+__device__ __forceinline__ float lz_add(float a, float b) { return a + b; }
+__device__ __forceinline__ double lz_add(double a, double b) { return a + b; }
+__device__ __forceinline__ df lz_fin(dfl a) { df r; eft_two_sum(a.s, a.e, r.hi, r.lo); return r; }
+__device__ __forceinline__ float lz_fin(float a) { return a; }
+__device__ __forceinline__ double lz_fin(double a) { return a; }
+__device__ __forceinline__ dfl shfl_xor(dfl a, int m) {
+  dfl r;
+  r.s = __shfl_xor_sync(0xffffffffu, a.s, m);
+  r.e = __shfl_xor_sync(0xffffffffu, a.e, m);
+  return r;
+}
+
+// ----------------------------------------------------------------------------
 // traits: zero, smallest positive normalised number (eps_FP of Alg. 6), and
 // conversions between storage and compute types.
 template <class C> struct Tr;

@@ -214,7 +214,9 @@ struct tt_server {
         if (cudaMemcpyAsync(&v, arena + r.arena_off, sizeof(int), cudaMemcpyDeviceToHost,
                             slot_stream[k]) == cudaSuccess &&
             cudaStreamSynchronize(slot_stream[k]) == cudaSuccess && v)
-          r.res.status = (v & DEV_ERR_SHAPE) ? TT_EINVAL : TT_ENUMERIC;
+          r.res.status = (v & DEV_ERR_SHAPE)     ? TT_EINVAL
+                         : (v & DEV_ERR_TIMEOUT) ? TT_ETIMEOUT
+                                                 : TT_ENUMERIC;
       }
       r.done = true;
       arena_free(r.arena_off, r.ws);

@@ -117,15 +117,20 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
   L.out = out;
   int64_t warps_cap;
   int cta_pr = 0, cta_nw = 0, cta_per_sm = 1;
-  const int cta_cfg = m_max > 16 ? tsqr_cta_pick(m_max, comp, &cta_pr, &cta_nw, &cta_per_sm) : -1;
+  int cta_kind = 3;
+  int cta_cfg = m_max > 16 ? tsqr_col_pick(m_max, in, comp, out, &cta_pr, &cta_nw, &cta_per_sm) : -1;
+  if (cta_cfg < 0) {
+    cta_kind = 2;
+    cta_cfg = m_max > 16 ? tsqr_cta_pick(m_max, comp, &cta_pr, &cta_nw, &cta_per_sm) : -1;
+  }
   if (cta_cfg >= 0) {
     // CTA-cooperative panels: one partial R per CTA
-    L.kind = 2;
+    L.kind = cta_kind;
     L.cfg = cta_cfg;
     L.maxm = m_max;
     L.pr = cta_pr;
     L.nw = cta_nw;
-    L.smem = tsqr_cta_smem(m_max, comp, cta_cfg);
+    L.smem = cta_kind == 3 ? tsqr_col_smem(m_max, comp, cta_cfg) : tsqr_cta_smem(m_max, comp, cta_cfg);
     L.panels = (rows + L.pr - 1) / L.pr;
     int64_t ctas;
     if (first) {
@@ -599,6 +604,7 @@ tt_status tt_last_device_status(const void* work, void* stream) {
   int v = 0;
   if (cudaMemcpy(&v, work, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TT_ECUDA;
   if (v & DEV_ERR_SHAPE) return TT_EINVAL;
+  if (v & DEV_ERR_TIMEOUT) return TT_ETIMEOUT;
   if (v & (DEV_SVD_NOCONV | DEV_NONFINITE)) return TT_ENUMERIC;
   return TT_OK;
 }

@@ -16,7 +16,11 @@ enum : int {
   DEV_ERR_SHAPE = 1,      // a kernel saw a shape outside what it was launched for
   DEV_SVD_NOCONV = 2,     // Jacobi SVD hit its sweep limit
   DEV_NONFINITE = 4,      // a non-finite singular value appeared
+  DEV_ERR_TIMEOUT = 8,    // a bounded in-kernel wait gave up (the kernel returned early)
 };
+
+// wait limit of in-kernel spin-waits, in SM clock cycles (~2 s at 2 GHz)
+constexpr long long kWaitCycles = 4000000000LL;
 
 // per-call device state (lives in the workspace)
 struct DevState {
@@ -38,8 +42,9 @@ constexpr int kMaxM = 512;     // widest unfolding handled
 // column-major output (ldR = warps * mb rows).
 struct TsqrLevel {
   int kind;          // 0 = narrow (warp, register panels), 1 = wide (warp, smem panels),
-                     // 2 = CTA-cooperative (register panels, R in shared memory)
-  int cfg;           // kind 2: layout id (see tsqr_cta.cu)
+                     // 2 = CTA-cooperative (register panels, R in shared memory),
+                     // 3 = column-owned CTA kernel (one barrier per column, look-ahead)
+  int cfg;           // kind 2: layout id (see tsqr_cta.cu); kind 3: see tsqr_col.cu
   int maxm;          // narrow: 4/8/16 ; wide: 32*chunks (template bound)
   int mmax;          // worst-case m of this level (<= maxm)
   int mval;          // m passed by value when the device pointer is null
@@ -62,6 +67,11 @@ int tsqr_cta_pick(int m_max, Fmt comp, int* pr, int* nw, int* per_sm);
 size_t tsqr_cta_smem(int m_max, Fmt comp, int id);
 // global-memory R scratch needed by layout `id` for `ctas` CTAs (0 if R sits in shared memory)
 size_t tsqr_cta_scratch(int m_max, Fmt comp, int id, int64_t ctas);
+// kind 3: layout id for m_max and the level's formats (or -1), rows per panel, warps, CTAs per SM
+int tsqr_col_pick(int m_max, Fmt in, Fmt comp, Fmt out, int* pr, int* nw, int* per_sm);
+size_t tsqr_col_smem(int m_max, Fmt comp, int id);
+cudaError_t launch_tsqr_col(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
+                            void* Rout, int64_t ldR, int* status, cudaStream_t s);
 cudaError_t launch_tsqr_cta(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
                             void* Rout, int64_t ldR, void* Rscr, int* status, cudaStream_t s);
 
