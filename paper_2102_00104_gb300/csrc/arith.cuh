@@ -156,6 +156,43 @@ __device__ __forceinline__ double lz_add(double a, double b) { return a + b; }
 __device__ __forceinline__ df lz_fin(dfl a) { df r; eft_two_sum(a.s, a.e, r.hi, r.lo); return r; }
 __device__ __forceinline__ float lz_fin(float a) { return a; }
 __device__ __forceinline__ double lz_fin(double a) { return a; }
+// acc + a*b with a lazy accumulator: TwoProd of the leading words, the cross terms
+// and both rounding errors go to the trailing word (12 FP32 instructions)
+__device__ __forceinline__ dfl lz_fmac(df a, df b, dfl acc) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float s, t;
+  eft_two_sum(acc.s, p, s, t);
+  dfl r;
+  r.s = s;
+  r.e = __fadd_rn(acc.e, __fadd_rn(e, t));
+  return r;
+}
+__device__ __forceinline__ float lz_fmac(float a, float b, float acc) { return __fmaf_rn(a, b, acc); }
+__device__ __forceinline__ double lz_fmac(double a, double b, double acc) { return __fma_rn(a, b, acc); }
+// c - a*b without the final renormalisation (12 FP32 instructions): the pair
+// (hi, lo) stays an exact-sum representation whose trailing word may reach a
+// few ulps of the leading one; every operation here accepts such pairs.  Used for
+// values that are updated many times (panel columns), renormalised when stored.
+__device__ __forceinline__ df fnmac_nr(df a, df b, df c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float s, t;
+  eft_two_sum(c.hi, -p, s, t);
+  return mkdf(s, __fadd_rn(__fsub_rn(c.lo, e), t));
+}
+// back to a normalised pair (hi = the FP32 rounding of the value).  A product
+// of two pairs drops lo*lo, which is only negligible when one factor is
+// normalised: pivot columns are renormalised before they are used.
+__device__ __forceinline__ df renorm(df a) { df r; eft_two_sum(a.hi, a.lo, r.hi, r.lo); return r; }
+__device__ __forceinline__ float renorm(float a) { return a; }
+__device__ __forceinline__ double renorm(double a) { return a; }
+__device__ __forceinline__ float fnmac_nr(float a, float b, float c) { return __fmaf_rn(-a, b, c); }
+__device__ __forceinline__ double fnmac_nr(double a, double b, double c) { return __fma_rn(-a, b, c); }
 __device__ __forceinline__ dfl shfl_xor(dfl a, int m) {
   dfl r;
   r.s = __shfl_xor_sync(0xffffffffu, a.s, m);

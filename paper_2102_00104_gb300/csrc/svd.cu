@@ -411,7 +411,7 @@ cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const i
                           int ldV, int* status, int* sweeps_out, cudaStream_t s) {
   // m > 48: spread the columns over a thread-block cluster when one fits
   int npl = 0;
-  const int nc = jacobi_cluster_plan(comp, m_max, &npl);
+  const int nc = tune_get("svd.cluster", 1) ? jacobi_cluster_plan(comp, m_max, &npl) : 0;
   if (nc > 0) {
     for (int cand : {nc, nc == 16 ? 8 : 16}) {
       const int np = cand == nc ? npl : jacobi_cluster_npl(comp, m_max, cand);

@@ -101,11 +101,12 @@ k_tsmm_rb(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
       ok[q] = row[q] < rows;
     }
     for (int c0 = 0; c0 < r; c0 += CPT) {
-      C acc[RPT][CPT];
+      // lazy float-float accumulators (normalised once, at the store)
+      decltype(lz(Tr<C>::zero())) acc[RPT][CPT];
 #pragma unroll
       for (int q = 0; q < RPT; ++q)
 #pragma unroll
-        for (int cc = 0; cc < CPT; ++cc) acc[q][cc] = Tr<C>::zero();
+        for (int cc = 0; cc < CPT; ++cc) acc[q][cc] = lz(Tr<C>::zero());
 #pragma unroll 8
       for (int k = 0; k < m; ++k) {
         C w[RPT];
@@ -117,7 +118,7 @@ k_tsmm_rb(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
         for (int cc = 0; cc < CPT; ++cc) {
           const C v = vk[cc];
 #pragma unroll
-          for (int q = 0; q < RPT; ++q) acc[q][cc] = fmac(w[q], v, acc[q][cc]);
+          for (int q = 0; q < RPT; ++q) acc[q][cc] = lz_fmac(w[q], v, acc[q][cc]);
         }
       }
 #pragma unroll
@@ -125,7 +126,7 @@ k_tsmm_rb(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
         if (c0 + cc < r)
 #pragma unroll
           for (int q = 0; q < RPT; ++q)
-            if (ok[q]) Y[row[q] + (int64_t)(c0 + cc) * ldy] = st_as<SO>(acc[q][cc]);
+            if (ok[q]) Y[row[q] + (int64_t)(c0 + cc) * ldy] = st_as<SO>(lz_fin(acc[q][cc]));
     }
   }
 }

@@ -26,20 +26,6 @@ const ColCfg kCol[15] = {
 
 using colk::run_col;
 
-cudaError_t run_first_df(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
-                         void* Rout, int64_t ldR, int* status, cudaStream_t s) {
-  using C = df;
-  using S = double;
-  switch (L.cfg) {
-    case 5: return run_col<12, 6, 8, 1, C, S, C>(L, W, ld, m_dev, Rout, ldR, status, s);
-    case 6: return run_col<16, 4, 4, 1, C, S, C>(L, W, ld, m_dev, Rout, ldR, status, s);
-    case 7: return run_col<16, 5, 6, 1, C, S, C>(L, W, ld, m_dev, Rout, ldR, status, s);
-    case 8: return run_col<8, 8, 4, 2, C, S, C>(L, W, ld, m_dev, Rout, ldR, status, s);
-    case 9: return run_col<8, 4, 8, 2, C, S, C>(L, W, ld, m_dev, Rout, ldR, status, s);
-    default: return colk::run_default<C, S, C>(L, W, ld, m_dev, Rout, ldR, status, s);
-  }
-}
-
 cudaError_t run_f32(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout,
                     int64_t ldR, int* status, cudaStream_t s) {
   using C = float;
@@ -76,7 +62,7 @@ int tsqr_col_pick(int m_max, Fmt in, Fmt comp, Fmt out, int* pr, int* nw, int* p
     else if (m_max <= 80) id = 2;
     else if (m_max <= 128) id = 3;
     else if (m_max <= 160) id = 4;
-    if (dfin && id >= 0) {
+    if ((dfin || dfup) && id >= 0) {
       // the autotuner may keep the row-group kernel for a bucket ("tsqr.col.<bucket>" = 0)
       char off[32];
       snprintf(off, sizeof(off), "tsqr.col.%d", id);
@@ -104,7 +90,7 @@ size_t tsqr_col_smem(int m_max, Fmt comp, int id) {
 cudaError_t launch_tsqr_col(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
                             void* Rout, int64_t ldR, int* status, cudaStream_t s) {
   if (L.in == Fmt::F64 && L.comp == Fmt::DF && L.out == Fmt::DF)
-    return run_first_df(L, W, ld, m_dev, Rout, ldR, status, s);
+    return colk::run_df_tuned<double>(L, W, ld, m_dev, Rout, ldR, status, s);
   if ((L.in == Fmt::DF && L.comp == Fmt::DF && L.out == Fmt::DF) ||
       (L.in == Fmt::F64 && L.comp == Fmt::F64 && L.out == Fmt::F64))
     return tsqr_col_upper(L, W, ld, m_dev, Rout, ldR, status, s);

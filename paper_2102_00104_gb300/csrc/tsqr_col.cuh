@@ -7,6 +7,11 @@
 //   column k of the panel belongs to warp  k mod NW  (slot c = k / NW);
 //   lane l of that warp holds rows  l + 32 q  (q < PRL) of it, PR = 32 PRL rows.
 //
+// Panel values are updated without renormalising the float-float pairs
+// (fnmac_nr) and dot products use lazy accumulators (lz_fmac); the pivot
+// column is renormalised before it is published, so every product has one
+// normalised factor (a product of two pairs drops lo*lo).
+//
 // So the dot products of Alg. 6 (pivot column with column k) never leave the
 // warp that owns column k: a butterfly reduce-scatter over the 32 lanes sums
 // all of the warp's active columns at once (about one add per column per lane).
@@ -124,24 +129,18 @@ __device__ __forceinline__ C butterfly(const C (&s)[V], int lane) {
   return lz_fin(z[0]);
 }
 
-// x . y over this lane's PRL rows, as two interleaved chains
+// x . y over this lane's PRL rows: two interleaved lazy float-float chains
 template <int PRL, class C>
 __device__ __forceinline__ C dot_rows(const C (&x)[PRL], const C (&y)[PRL]) {
-  if constexpr (PRL >= 4) {
-    C a0 = mul(x[0], y[0]), a1 = mul(x[1], y[1]);
+  auto a0 = lz(Tr<C>::zero());
+  auto a1 = lz(Tr<C>::zero());
 #pragma unroll
-    for (int q = 2; q + 1 < PRL; q += 2) {
-      a0 = fmac(x[q], y[q], a0);
-      a1 = fmac(x[q + 1], y[q + 1], a1);
-    }
-    if constexpr (PRL % 2) a0 = fmac(x[PRL - 1], y[PRL - 1], a0);
-    return add(a0, a1);
-  } else {
-    C a0 = mul(x[0], y[0]);
-#pragma unroll
-    for (int q = 1; q < PRL; ++q) a0 = fmac(x[q], y[q], a0);
-    return a0;
+  for (int q = 0; q + 1 < PRL; q += 2) {
+    a0 = lz_fmac(x[q], y[q], a0);
+    a1 = lz_fmac(x[q + 1], y[q + 1], a1);
   }
+  if constexpr (PRL % 2) a0 = lz_fmac(x[PRL - 1], y[PRL - 1], a0);
+  return lz_fin(lz_add(a0, a1));
 }
 
 // Reflector of column jn (Alg. 6) from the column's panel values x (after all
@@ -215,7 +214,7 @@ __device__ __forceinline__ bool col_step(C (&a)[CLW][PRL], int j, int jj, uint32
     const C c = mul(fmac(piv, r, d), rt);
     if (lane == 0) R[rj + 1] = fnmac(c, piv, r);
 #pragma unroll
-    for (int q = 0; q < PRL; ++q) x[q] = fnmac(c, pv[q], x[q]);
+    for (int q = 0; q < PRL; ++q) x[q] = renorm(fnmac_nr(c, pv[q], x[q]));
     if (same) {
 #pragma unroll
       for (int q = 0; q < PRL; ++q) a[JB][q] = x[q];
@@ -252,13 +251,13 @@ __device__ __forceinline__ bool col_step(C (&a)[CLW][PRL], int j, int jj, uint32
   if (first_live) {
     const C cb = shfl_idx(ck, 0);
 #pragma unroll
-    for (int q = 0; q < PRL; ++q) a[JB][q] = fnmac(cb, pv[q], a[JB][q]);
+    for (int q = 0; q < PRL; ++q) a[JB][q] = fnmac_nr(cb, pv[q], a[JB][q]);
   }
 #pragma unroll
   for (int c = JB + 1; c < CLW; ++c) {
     const C cb = shfl_idx(ck, (c - JB) << (5 - L));
 #pragma unroll
-    for (int q = 0; q < PRL; ++q) a[c][q] = fnmac(cb, pv[q], a[c][q]);
+    for (int q = 0; q < PRL; ++q) a[c][q] = fnmac_nr(cb, pv[q], a[c][q]);
   }
   return true;
 }
@@ -389,6 +388,20 @@ cudaError_t run_default(const TsqrLevel& L, const void* W, int64_t ld, const int
     case 3: return run_col<16, 8, 4, 1, C, S, RO>(L, W, ld, m_dev, Rout, ldR, status, s);
     case 4: return run_col<20, 8, 3, 1, C, S, RO>(L, W, ld, m_dev, Rout, ldR, status, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+// defaults and the autotuner's alternatives (ids 5-9) of the float-float arithmetic
+template <class S>
+cudaError_t run_df_tuned(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout,
+                         int64_t ldR, int* status, cudaStream_t s) {
+  switch (L.cfg) {
+    case 5: return run_col<12, 6, 8, 1, df, S, df>(L, W, ld, m_dev, Rout, ldR, status, s);
+    case 6: return run_col<16, 4, 4, 1, df, S, df>(L, W, ld, m_dev, Rout, ldR, status, s);
+    case 7: return run_col<16, 5, 6, 1, df, S, df>(L, W, ld, m_dev, Rout, ldR, status, s);
+    case 8: return run_col<8, 8, 4, 2, df, S, df>(L, W, ld, m_dev, Rout, ldR, status, s);
+    case 9: return run_col<8, 4, 8, 2, df, S, df>(L, W, ld, m_dev, Rout, ldR, status, s);
+    default: return run_default<df, S, df>(L, W, ld, m_dev, Rout, ldR, status, s);
   }
 }
 

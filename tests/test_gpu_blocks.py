@@ -34,7 +34,7 @@ def sv(M):
 # tails, several panels per warp, several TSQR levels and wide (rows < m) cases
 TSQR_CASES = [(1, 1), (37, 1), (1000, 3), (4096, 4), (5000, 5), (70000, 8), (9, 8), (12345, 13),
               (3000, 16), (2049, 17), (20000, 32), (6000, 40), (100000, 64), (3000, 80), (50, 100),
-              (5000, 160), (700, 257), (1500, 400)]
+              (5000, 160), (700, 257), (1500, 400), (9, 64), (30, 80), (100, 128)]
 
 
 @pytest.mark.parametrize("rows,m", TSQR_CASES)
@@ -79,6 +79,19 @@ def test_tsqr_rank_deficient_and_zero_columns():
     assert np.all(s[3:] <= 1e-12 * s[0])
     Z = api.tsqr(colmajor(np.zeros((1000, 5)))).cpu().numpy()
     assert np.all(np.isfinite(Z)) and np.max(np.abs(Z)) < 1e-15
+
+
+@pytest.mark.parametrize("m,rank", [(64, 10), (80, 10), (128, 7), (32, 3)])
+def test_tsqr_low_rank_wide_panels(m, rank):
+    # exactly low-rank W: after `rank` reflectors the panel columns hold only rounding
+    # noise, which the float-float updates must keep at noise level (no growth, no NaN)
+    rng = np.random.default_rng(m + rank)
+    W = rng.standard_normal((40000, rank)) @ rng.standard_normal((rank, m))
+    R = api.tsqr(colmajor(W)).cpu().numpy()
+    assert np.all(np.isfinite(R))
+    s, s_ref = sv(R), sv(W)
+    assert np.max(np.abs(s - s_ref)) <= 1e-12 * s_ref[0]
+    assert np.all(s[rank:] <= 1e-12 * s[0])
 
 
 @pytest.mark.parametrize("m", [1, 2, 3, 8, 17, 40, 64, 80, 131, 160, 257, 400])
