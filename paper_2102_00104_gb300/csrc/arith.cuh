@@ -193,6 +193,21 @@ __device__ __forceinline__ float renorm(float a) { return a; }
 __device__ __forceinline__ double renorm(double a) { return a; }
 __device__ __forceinline__ float fnmac_nr(float a, float b, float c) { return __fmaf_rn(-a, b, c); }
 __device__ __forceinline__ double fnmac_nr(double a, double b, double c) { return __fma_rn(-a, b, c); }
+__device__ __forceinline__ dfl shfl_xor_m(dfl a, int m, unsigned mask) {
+  dfl r;
+  r.s = __shfl_xor_sync(mask, a.s, m);
+  r.e = __shfl_xor_sync(mask, a.e, m);
+  return r;
+}
+__device__ __forceinline__ double shfl_xor_m(double a, int m, unsigned mask) { return __shfl_xor_sync(mask, a, m); }
+__device__ __forceinline__ float shfl_xor_m(float a, int m, unsigned mask) { return __shfl_xor_sync(mask, a, m); }
+// lazy sum over an aligned group of G lanes (G divides 32; mask = the group's lanes)
+template <int G, class Z>
+__device__ __forceinline__ Z lz_gsum(Z a, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) a = lz_add(a, shfl_xor_m(a, o, mask));
+  return a;
+}
 __device__ __forceinline__ dfl shfl_xor(dfl a, int m) {
   dfl r;
   r.s = __shfl_xor_sync(0xffffffffu, a.s, m);

@@ -168,21 +168,21 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
         }
         C* ap = A + (size_t)p * ldA;
         C* aq = A + (size_t)q * ldA;
-        C al = Tr<C>::zero(), be = Tr<C>::zero(), ga = Tr<C>::zero();
+        auto al = lz(Tr<C>::zero()), be = al, ga = al;  // lazy float-float sums
         for (int i = gl; i < m; i += G) {
           const C x = ap[i], y = aq[i];
-          al = fmac(x, x, al);
-          be = fmac(y, y, be);
-          ga = fmac(x, y, ga);
+          al = lz_fmac(x, x, al);
+          be = lz_fmac(y, y, be);
+          ga = lz_fmac(x, y, ga);
         }
-        al = gsum<G>(al, gmask);
-        be = gsum<G>(be, gmask);
-        ga = gsum<G>(ga, gmask);
-        const float gf = fabsf(fp32_hi(ga));
-        const float nf = sqrtf(fp32_hi(al)) * sqrtf(fp32_hi(be));
+        const C alf = lz_fin(lz_gsum<G>(al, gmask));
+        const C bef = lz_fin(lz_gsum<G>(be, gmask));
+        const C gaf = lz_fin(lz_gsum<G>(ga, gmask));
+        const float gf = fabsf(fp32_hi(gaf));
+        const float nf = sqrtf(fp32_hi(alf)) * sqrtf(fp32_hi(bef));
         if (gf > tol * nf && nf > floor_abs && gf > 0.f) {
           // zeta = (beta - alpha) / (2 gamma): difference in working precision, quotient in FP32
-          const float zf = fp32_hi(sub(be, al)) / (2.f * fp32_hi(ga));
+          const float zf = fp32_hi(sub(bef, alf)) / (2.f * fp32_hi(gaf));
           const float az = fabsf(zf);
           float tf = az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f)));
           if (zf < 0.f) tf = -tf;

@@ -171,20 +171,20 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
       for (int i = gid; i < npl; i += ngroups) {
         C* ap = Acol + (size_t)tslot[i] * m_max;
         C* aq = Acol + (size_t)bslot[i] * m_max;
-        C al = Tr<C>::zero(), be = Tr<C>::zero(), ga = Tr<C>::zero();
+        auto al = lz(Tr<C>::zero()), be = al, ga = al;  // lazy float-float sums
         for (int r = gl; r < m; r += G) {
           const C x = ap[r], y = aq[r];
-          al = fmac(x, x, al);
-          be = fmac(y, y, be);
-          ga = fmac(x, y, ga);
+          al = lz_fmac(x, x, al);
+          be = lz_fmac(y, y, be);
+          ga = lz_fmac(x, y, ga);
         }
-        al = gsum2<G>(al, gmask);
-        be = gsum2<G>(be, gmask);
-        ga = gsum2<G>(ga, gmask);
-        const float gf = fabsf(hi32(ga));
-        const float nf = sqrtf(hi32(al)) * sqrtf(hi32(be));
+        const C alf = lz_fin(lz_gsum<G>(al, gmask));
+        const C bef = lz_fin(lz_gsum<G>(be, gmask));
+        const C gaf = lz_fin(lz_gsum<G>(ga, gmask));
+        const float gf = fabsf(hi32(gaf));
+        const float nf = sqrtf(hi32(alf)) * sqrtf(hi32(bef));
         if (gf > tol * nf && nf > floor_abs && gf > 0.f) {
-          const float zf = hi32(sub(be, al)) / (2.f * hi32(ga));
+          const float zf = hi32(sub(bef, alf)) / (2.f * hi32(gaf));
           const float az = fabsf(zf);
           float tf = az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f)));
           if (zf < 0.f) tf = -tf;
