@@ -85,6 +85,11 @@ cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const i
 size_t jacobi_scratch_bytes(Fmt comp, int m_max);
 // cluster form (svd_cluster.cu): cluster size for m (0 = single CTA) and its launch
 int jacobi_cluster_plan(Fmt comp, int m_max, int* npl_out);
+// block-cyclic cluster kernel: cluster size (0 if it does not apply) and columns per block
+int jacobi_block_plan(Fmt comp, int m_max, int* npl_out);
+cudaError_t launch_jacobi_block(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
+                                int m_max, int nc, int npl, double* sigma, void* Vout, int ldV,
+                                int* status, int* sweeps_out, cudaStream_t s);
 int jacobi_cluster_npl(Fmt comp, int m_max, int nc);
 cudaError_t launch_jacobi_cluster(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
                                   int m_max, int nc, int npl, double* sigma, void* Vout, int ldV,

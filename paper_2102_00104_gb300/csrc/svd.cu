@@ -409,7 +409,18 @@ static void run_jacobi(const void* R, int64_t ldR, const int* m_dev, int m_max, 
 cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
                           int m_max, void* Ag, void* Vg, int ldA, double* sigma, void* Vout,
                           int ldV, int* status, int* sweeps_out, cudaStream_t s) {
-  // m > 48: spread the columns over a thread-block cluster when one fits
+  // m > 48: spread the columns over a thread-block cluster when one fits; the block-cyclic
+  // ordering first, then the ring ordering
+  if (m_max > 48 && tune_get("svd.block", 1)) {
+    int bnpl = 0;
+    const int bnc = jacobi_block_plan(comp, m_max, &bnpl);
+    if (bnc > 0) {
+      const cudaError_t e = launch_jacobi_block(comp, rin, R, ldR, m_dev, m_max, bnc, bnpl, sigma,
+                                                Vout, ldV, status, sweeps_out, s);
+      if (e == cudaSuccess) return e;
+      cudaGetLastError();  // launch refused (no resident cluster of that size)
+    }
+  }
   int npl = 0;
   const int nc = tune_get("svd.cluster", 1) ? jacobi_cluster_plan(comp, m_max, &npl) : 0;
   if (nc > 0) {

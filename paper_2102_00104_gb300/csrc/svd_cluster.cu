@@ -318,6 +318,256 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
   cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
+// ---- block-cyclic ordering ----------------------------------------------------------------
+// The MP = 2 NC npl columns (m padded with zero columns; npl even) form 2 NC blocks of npl
+// columns; CTA c holds a top and a bottom block.  A sweep is the circle method on blocks,
+// 2 NC - 1 outer rounds: in each, npl cross rounds pair top_i with bottom_{(i+k) mod npl}
+// (k = 0..npl-1), and in the first outer round every CTA also pairs the columns inside its
+// two blocks (npl - 1 rounds of the circle method inside a block).  Every pair of columns
+// meets once per sweep, only __syncthreads separates the inner rounds, and whole blocks
+// move between CTAs (distributed shared memory, one cluster barrier) once per outer round.
+// Blocks live in four buffers: top = 2p, bottom = 2p + 1 for the parity p of the outer
+// round; the moves of an outer round write the other parity's buffers (remote or local).
+
+// rotate the pair (a_p, a_q) (and V's columns) by a group of G lanes; true if rotated
+template <class C, int G>
+__device__ __forceinline__ bool jacobi_pair(C* ap, C* aq, C* vp, C* vq, int m, int gl,
+                                            unsigned gmask, float tol, float floor_abs) {
+  auto al = lz(Tr<C>::zero()), be = al, ga = al;
+  for (int r = gl; r < m; r += G) {
+    const C x = ap[r], y = aq[r];
+    al = lz_fmac(x, x, al);
+    be = lz_fmac(y, y, be);
+    ga = lz_fmac(x, y, ga);
+  }
+  const C alf = lz_fin(lz_gsum<G>(al, gmask));
+  const C bef = lz_fin(lz_gsum<G>(be, gmask));
+  const C gaf = lz_fin(lz_gsum<G>(ga, gmask));
+  const float gf = fabsf(hi32(gaf));
+  const float nf = sqrtf(hi32(alf)) * sqrtf(hi32(bef));
+  if (!(gf > tol * nf && nf > floor_abs && gf > 0.f)) return false;
+  const float zf = hi32(sub(bef, alf)) / (2.f * hi32(gaf));
+  const float az = fabsf(zf);
+  float tf = az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f)));
+  if (zf < 0.f) tf = -tf;
+  C cs, sn;
+  rotcs(tf, cs, sn);
+  for (int r = gl; r < m; r += G) {
+    const C x = ap[r], y = aq[r];
+    ap[r] = fnmac(sn, y, mul(cs, x));
+    aq[r] = fmac(sn, x, mul(cs, y));
+    const C vx = vp[r], vy = vq[r];
+    vp[r] = fnmac(sn, vy, mul(cs, vx));
+    vq[r] = fmac(sn, vx, mul(cs, vy));
+  }
+  return true;
+}
+
+template <class C, class RI, int G>
+__global__ void __launch_bounds__(1024)
+k_jacobi_block(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, int m_max,
+               int npl, double* __restrict__ sigma, C* __restrict__ Vout, int ldV, int* status,
+               int* sweeps_out, int max_sweeps) {
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_rot;
+  __shared__ int s_flags[2][16];
+  __shared__ float s_red[32];
+  __shared__ int s_any;
+  __shared__ float s_fro;
+  const int m = m_ptr ? *m_ptr : m_max;
+  const int NC = (int)cl.num_blocks();
+  const int c = (int)cl.block_rank();
+  const int MP = 2 * NC * npl;
+  if (m < 1 || m > m_max || MP < m || (npl & 1) || npl < 2 || NC < 2 || NC > 16 ||
+      (int)blockDim.x < npl * G) {
+    if (threadIdx.x == 0 && c == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
+    return;  // uniform over the cluster
+  }
+  const size_t bs = (size_t)npl * m_max;                 // one block: column i at i * m_max
+  C* Ab = reinterpret_cast<C*>(smem_raw);                // buffer b at Ab + b * bs
+  C* Vb = Ab + 4 * bs;
+  int* cid = reinterpret_cast<int*>(Vb + 4 * bs);        // cid[b * npl + i]
+  double* allnorm = reinterpret_cast<double*>(cid + ((4 * npl + 1) & ~1));  // [MP]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nwarps = nt >> 5;
+
+  // power-of-two scaling from max |R| (every CTA reads all of R) and ||R||_F^2 in FP32
+  float mx = 0.f, fro = 0.f;
+  for (int idx = tid; idx < m * m; idx += nt) {
+    const int i = idx % m, k = idx / m;
+    if (i <= k) mx = fmaxf(mx, fabsf(hi32(ld_as<C>(R[i + (int64_t)k * ldR]))));
+  }
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) s_red[wid] = mx;
+  __syncthreads();
+  float t = 0.f;
+  for (int w = 0; w < nwarps; ++w) t = fmaxf(t, s_red[w]);
+  int ex = 0;
+  if (t > 0.f) frexpf(t, &ex);
+  __syncthreads();
+  // initial blocks: top = block 2c (buffer 0), bottom = block 2c+1 (buffer 1)
+  for (int b = 0; b < 2; ++b) {
+    for (int i = 0; i < npl; ++i) {
+      const int col = (2 * c + b) * npl + i;
+      if (tid == 0) cid[b * npl + i] = col;
+      C* a = Ab + b * bs + (size_t)i * m_max;
+      C* v = Vb + b * bs + (size_t)i * m_max;
+      for (int r = tid; r < m; r += nt) {
+        C x = Tr<C>::zero();
+        if (col < m && r <= col) {
+          x = pow2s<C>(ld_as<C>(R[r + (int64_t)col * ldR]), -ex);
+          const float f = hi32(x);
+          fro = fmaf(f, f, fro);
+        }
+        a[r] = x;
+        v[r] = (r == col) ? Tr<C>::one() : Tr<C>::zero();
+      }
+    }
+  }
+  // every CTA needs the whole ||A||_F^2: the local parts, read from every CTA after the
+  // first cluster barrier (which also makes every CTA's shared memory addressable)
+  for (int o = 16; o; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+  if (lane == 0) s_red[wid] = fro;
+  __syncthreads();
+  if (tid == 0) {
+    float f = 0.f;
+    for (int w = 0; w < nwarps; ++w) f += s_red[w];
+    s_fro = f;
+  }
+  cl.sync();
+  float frot = 0.f;
+  for (int q = 0; q < NC; ++q) frot += *cl.map_shared_rank(&s_fro, q);
+  const float tol = ctol<C>(m);
+  const float floor_abs = tol * tol * frot;
+  const int gid = tid / G, gl = tid % G, ngroups = nt / G;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  int* flags0 = cl.map_shared_rank(&s_flags[0][0], 0);
+  const int half = npl / 2;
+
+  int og = 0;  // outer rounds so far (buffer parity)
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    int rot = 0;
+    for (int o = 0; o < 2 * NC - 1; ++o, ++og) {
+      const int p = og & 1;
+      C* TA = Ab + (2 * p) * bs;
+      C* TV = Vb + (2 * p) * bs;
+      C* BA = Ab + (2 * p + 1) * bs;
+      C* BV = Vb + (2 * p + 1) * bs;
+      if (o == 0) {
+        // pairs inside the top and the bottom block: circle method on npl columns
+        for (int k = 0; k < npl - 1; ++k) {
+          for (int u = gid; u < npl; u += ngroups) {
+            C* XA = u < half ? TA : BA;
+            C* XV = u < half ? TV : BV;
+            const int i = u < half ? u : u - half;
+            int x, y;
+            if (i == 0) {
+              x = npl - 1;
+              y = k;
+            } else {
+              x = (k + i) % (npl - 1);
+              y = (k - i + npl - 1) % (npl - 1);
+            }
+            rot |= jacobi_pair<C, G>(XA + (size_t)x * m_max, XA + (size_t)y * m_max,
+                                     XV + (size_t)x * m_max, XV + (size_t)y * m_max, m, gl, gmask,
+                                     tol, floor_abs);
+          }
+          __syncthreads();
+        }
+      }
+      // cross pairs (top_u, bottom_{(u+k) mod npl})
+      for (int k = 0; k < npl; ++k) {
+        for (int u = gid; u < npl; u += ngroups) {
+          const int w2 = (u + k) % npl;
+          rot |= jacobi_pair<C, G>(TA + (size_t)u * m_max, BA + (size_t)w2 * m_max,
+                                   TV + (size_t)u * m_max, BV + (size_t)w2 * m_max, m, gl, gmask,
+                                   tol, floor_abs);
+        }
+        __syncthreads();
+      }
+      const bool last = o == 2 * NC - 2;
+      if (last) {
+        // any rotation in this sweep: one flag per CTA into CTA 0 (read after the barrier)
+        if (rot && gl == 0) s_rot = 1;
+        __syncthreads();
+        if (tid == 0) flags0[(sweep & 1) * 16 + c] = s_rot;
+      }
+      // move the blocks (circle method on blocks) into the other parity's buffers
+      const int q = 1 - p;
+      auto put = [&](int rank, int dst, const C* sA, const C* sV, const int* sc) {
+        C* dA = cl.map_shared_rank(Ab, rank) + (size_t)dst * bs;
+        C* dV = cl.map_shared_rank(Vb, rank) + (size_t)dst * bs;
+        int* dc = cl.map_shared_rank(cid, rank) + dst * npl;
+        for (int idx = tid; idx < npl * m; idx += nt) {
+          const size_t off = (size_t)(idx / m) * m_max + idx % m;
+          dA[off] = sA[off];
+          dV[off] = sV[off];
+        }
+        for (int i = tid; i < npl; i += nt) dc[i] = sc[i];
+      };
+      const int* Tc = cid + (2 * p) * npl;
+      const int* Bc = cid + (2 * p + 1) * npl;
+      if (c == 0) {
+        put(0, 2 * q, TA, TV, Tc);          // top(0) stays
+        put(1, 2 * q, BA, BV, Bc);          // bottom(0) -> top(1)
+      } else if (c < NC - 1) {
+        put(c + 1, 2 * q, TA, TV, Tc);      // top(c) -> top(c+1)
+        put(c - 1, 2 * q + 1, BA, BV, Bc);  // bottom(c) -> bottom(c-1)
+      } else {
+        put(c - 1, 2 * q + 1, BA, BV, Bc);  // bottom(NC-1) -> bottom(NC-2)
+        put(c, 2 * q + 1, TA, TV, Tc);      // top(NC-1) -> bottom(NC-1)
+      }
+      cl.sync();
+    }
+    if (tid == 0) {
+      int any = 0;
+      for (int k = 0; k < NC; ++k) any |= flags0[(sweep & 1) * 16 + k];
+      s_any = any;
+    }
+    __syncthreads();
+    if (s_any == 0) break;
+  }
+  if (sweep >= max_sweeps && tid == 0 && c == 0 && status) atomicOr(status, DEV_SVD_NOCONV);
+  if (tid == 0 && c == 0 && sweeps_out) *sweeps_out = sweep + 1;
+
+  // norms of every column into every CTA, then rank and write the local columns
+  const int p = og & 1;
+  for (int k = wid; k < 2 * npl; k += nwarps) {
+    const C* a = Ab + (2 * p + k / npl) * bs + (size_t)(k % npl) * m_max;
+    auto acc = lz(Tr<C>::zero());
+    for (int r = lane; r < m; r += 32) acc = lz_fmac(a[r], a[r], acc);
+    const C nk = lz_fin(lz_gsum<32>(acc, 0xffffffffu));
+    if (lane == 0) {
+      const int id = cid[(2 * p + k / npl) * npl + k % npl];
+      const double nv = to_f64(nk);
+      for (int q = 0; q < NC; ++q) cl.map_shared_rank(allnorm, q)[id] = nv;
+    }
+  }
+  cl.sync();
+  for (int k = tid; k < 2 * npl; k += nt) {
+    const int b = 2 * p + k / npl, i = k % npl;
+    const int id = cid[b * npl + i];
+    if (id >= m) continue;  // padding column
+    const double nk = allnorm[id];
+    int rank = 0;
+    for (int k2 = 0; k2 < m; ++k2) {
+      if (k2 == id) continue;
+      const double n2 = allnorm[k2];
+      if (n2 > nk || (n2 == nk && k2 < id)) ++rank;
+    }
+    const double sg = ldexp(sqrt(nk), ex);
+    if (!isfinite(sg) && status) atomicOr(status, DEV_NONFINITE);
+    sigma[rank] = sg;
+    const C* v = Vb + b * bs + (size_t)i * m_max;
+    for (int r = 0; r < m; ++r) Vout[r + (size_t)rank * ldV] = v[r];
+  }
+  cl.sync();  // no CTA leaves while others may still write its shared memory
+}
+
 std::mutex g_cl_mu;
 int g_cl_ok[2][17];  // [type][NC]: 0 unknown, 1 usable, -1 not usable
 
@@ -411,6 +661,109 @@ cudaError_t launch_jacobi_cluster(Fmt comp, Fmt rin, const void* R, int64_t ldR,
   if (comp == Fmt::F64 && rin == Fmt::F64)
     return wide ? launch_cl<double, double, 32>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV, status, sweeps_out, s)
                 : launch_cl<double, double, 16>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV, status, sweeps_out, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace tt
+
+namespace tt {
+
+namespace {
+
+std::mutex g_blk_mu;
+int g_blk_ok[2][17][8];  // [type][NC][smem bucket of 32 KB]: 0 unknown, 1 usable, -1 not
+
+size_t jacobi_block_smem(Fmt comp, int m_max, int nc, int npl) {
+  return (size_t)8 * npl * m_max * fmt_bytes(comp) + (size_t)((4 * npl + 1) & ~1) * 4 +
+         (size_t)2 * nc * npl * sizeof(double) + 16;
+}
+
+template <class C, class RI, int G>
+cudaError_t launch_blk(const void* R, int64_t ldR, const int* m_dev, int m_max, int nc, int npl,
+                       size_t smem, double* sigma, void* Vout, int ldV, int* status,
+                       int* sweeps_out, cudaStream_t s) {
+  auto k = k_jacobi_block<C, RI, G>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (nc > 8) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  int threads = ((npl * G + 31) / 32) * 32;
+  if (threads < 64) threads = 64;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nc, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  {
+    std::lock_guard<std::mutex> lk(g_blk_mu);
+    const int bucket = (int)std::min<size_t>(7, smem / (32 * 1024));
+    int& ok = g_blk_ok[std::is_same<C, df>::value ? 0 : 1][nc][bucket];
+    if (ok == 0) {
+      int nclusters = 0;
+      ok = (cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg) == cudaSuccess && nclusters > 0) ? 1 : -1;
+      cudaGetLastError();
+    }
+    if (ok < 0) return cudaErrorNotSupported;
+  }
+  return cudaLaunchKernelEx(&cfg, k, static_cast<const RI*>(R), ldR, m_dev, m_max, npl, sigma,
+                            static_cast<C*>(Vout), ldV, status, sweeps_out, 60);
+}
+
+}  // namespace
+
+// Cluster size and block width for the block-cyclic kernel: minimises a per-sweep cost of
+// rounds x max(latency of a round, arithmetic of a round) + one block move per outer round
+// (all in microseconds, measured orders of magnitude on GB300); 0 if nothing fits.
+int jacobi_block_plan(Fmt comp, int m_max, int* npl_out) {
+  const int forced = tune_get("svd.block_nc", 0);
+  double best = 1e30;
+  int best_nc = 0, best_npl = 0;
+  for (int nc : {2, 4, 8, 16}) {
+    if (forced && nc != forced) continue;
+    int npl = (m_max + 2 * nc - 1) / (2 * nc);
+    npl += npl & 1;
+    if (npl < 2) npl = 2;
+    if (npl * (m_max > 96 ? 32 : 16) > 1024) continue;
+    if (jacobi_block_smem(comp, m_max, nc, npl) > 220 * 1024) continue;
+    const double rounds = (npl - 1) + (2.0 * nc - 1) * npl;
+    const double work = npl * (double)m_max * 124.0 / 128.0 / 2000.0;  // us per round
+    const double lat = 0.3 + (double)m_max / (m_max > 96 ? 32.0 : 16.0) * 0.06;  // us per round
+    const double cost = rounds * std::max(lat, work) + (2 * nc - 1) * 1.5;
+    if (cost < best) {
+      best = cost;
+      best_nc = nc;
+      best_npl = npl;
+    }
+  }
+  if (best_nc) *npl_out = best_npl;
+  return best_nc;
+}
+
+cudaError_t launch_jacobi_block(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
+                                int m_max, int nc, int npl, double* sigma, void* Vout, int ldV,
+                                int* status, int* sweeps_out, cudaStream_t s) {
+  const size_t smem = jacobi_block_smem(comp, m_max, nc, npl);
+  // lanes per pair: 16 up to m = 96, else a warp (measured on GB300)
+  const bool wide = m_max > 96;
+#define TT_BLK(C, RI)                                                                            \
+  return wide ? launch_blk<C, RI, 32>(R, ldR, m_dev, m_max, nc, npl, smem, sigma, Vout, ldV,     \
+                                      status, sweeps_out, s)                                     \
+              : launch_blk<C, RI, 16>(R, ldR, m_dev, m_max, nc, npl, smem, sigma, Vout, ldV,     \
+                                      status, sweeps_out, s)
+  if (comp == Fmt::DF && rin == Fmt::DF) TT_BLK(df, df);
+  if (comp == Fmt::DF && rin == Fmt::F32) TT_BLK(df, float);
+  if (comp == Fmt::DF && rin == Fmt::F64) TT_BLK(df, double);
+  if (comp == Fmt::F64 && rin == Fmt::F64) TT_BLK(double, double);
+#undef TT_BLK
   return cudaErrorInvalidValue;
 }
 
