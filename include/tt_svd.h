@@ -115,6 +115,26 @@ tt_status tt_svd_ex(const void* X, tt_dtype dt, int d, const int64_t* n, int r_m
                     double* err2_out, void* work, size_t work_bytes, void* stream,
                     const tt_opts* opts);
 
+/* tt_svd_from_host: tt_svd_ex with X in HOST memory (n_1*...*n_d elements of type
+ * dt, Fortran order; pinned memory for the copy to overlap, pageable memory works
+ * but serialises).  The library copies X into X_dev (caller-owned device buffer of
+ * the same size) on an internal stream forked from `stream`, in `chunks` row blocks
+ * of the first unfolding that is not elided (0 = 16 blocks), and runs the first TSQR
+ * level (Alg. 2 line 5, Sec. 3.2) on each block as soon as that block has arrived;
+ * the partial R's of all blocks enter the same reduction tree, so the result equals
+ * tt_svd_ex up to the order of the tree.  When every step is elided X is copied in
+ * one piece.  work: at least tt_query_from_host's work_bytes (256-byte aligned).
+ * Asynchronous on `stream`: X_host must stay valid and unchanged until `stream`
+ * has passed this call.  Argument errors: TT_EINVAL (null pointers, chunks outside
+ * 0..4096); TT_ENOMEM if work_bytes is too small; TT_ECUDA if the copy stream
+ * cannot be created. */
+tt_status tt_query_from_host(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
+                             int chunks, size_t* work_bytes);
+tt_status tt_svd_from_host(const void* X_host, void* X_dev, tt_dtype dt, int d, const int64_t* n,
+                           int r_max, double tol, int chunks, double* const* cores_out,
+                           int64_t* ranks_out, double* sigma_out, double* err2_out, void* work,
+                           size_t work_bytes, void* stream, const tt_opts* opts);
+
 /* Reads the device status word left by the last tt_svd* call that used `work`
  * (synchronising `stream` first).  TT_OK if no device-side failure was seen. */
 tt_status tt_last_device_status(const void* work, void* stream);

@@ -54,6 +54,10 @@ class TTSVDPlan:
         self.dt = _DT[dtype]
         self.opts = capi.tt_opts(_ARITH[arith], 1 if no_elide else 0, int(tsqr_ctas))
         _, self.work_bytes = capi.tt_query(self.d, self.dims, self.r_max, self.tol, self.dt)
+        # also large enough for run_host (first TSQR level in row blocks)
+        self.work_bytes = max(self.work_bytes, capi.tt_query_from_host(
+            self.d, self.dims, self.r_max, self.tol, self.dt, 0))
+        self.X_dev = None
         self.caps, self.sig_stride, sig_count = capi.tt_core_caps(self.d, self.dims, self.r_max)
         dev = torch.device(device)
         self.work = torch.empty(max(256, self.work_bytes) + 256, dtype=torch.uint8, device=dev)
@@ -73,6 +77,27 @@ class TTSVDPlan:
         capi.tt_svd(X.data_ptr(), self.dt, self.d, self.dims, self.r_max, self.tol, self._core_ptrs,
                     self.ranks.data_ptr(), self.sigma.data_ptr() if self.sigma is not None else None,
                     self.err2.data_ptr(), self.work_ptr, self.work_bytes, _stream_ptr(stream), self.opts)
+
+    def run_host(self, X_host: torch.Tensor, stream=None, chunks: int = 0) -> None:
+        """Same TT-SVD with X in (pinned) host memory: the copy to the device overlaps the
+        first TSQR level, block by block (tt_svd_from_host)."""
+        if X_host.is_cuda or X_host.dtype != self.dtype or not X_host.is_contiguous():
+            raise ValueError("X_host must be a contiguous CPU tensor of the plan's dtype")
+        if X_host.numel() != int(torch.tensor(self.dims).prod()):
+            raise ValueError("X_host does not have prod(dims) entries")
+        if self.X_dev is None:
+            self.X_dev = torch.empty(X_host.numel(), dtype=self.dtype, device=self.work.device)
+        need = capi.tt_query_from_host(self.d, self.dims, self.r_max, self.tol, self.dt, int(chunks))
+        if need > self.work_bytes:  # more row blocks keep more partial R's
+            torch.cuda.current_stream(self.work.device).synchronize()
+            self.work = torch.empty(need + 256, dtype=torch.uint8, device=self.work.device)
+            self.work_ptr = (self.work.data_ptr() + 255) & ~255
+            self.work_bytes = need
+        capi.tt_svd_from_host(X_host.data_ptr(), self.X_dev.data_ptr(), self.dt, self.d, self.dims,
+                              self.r_max, self.tol, int(chunks), self._core_ptrs, self.ranks.data_ptr(),
+                              self.sigma.data_ptr() if self.sigma is not None else None,
+                              self.err2.data_ptr(), self.work_ptr, self.work_bytes, _stream_ptr(stream),
+                              self.opts)
 
     def device_status(self, stream=None) -> int:
         return capi.tt_last_device_status(self.work_ptr, _stream_ptr(stream))

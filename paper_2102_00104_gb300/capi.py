@@ -25,7 +25,8 @@ EXPORTED = ["tt_query", "tt_core_caps", "tt_svd", "tt_svd_ex", "tt_last_device_s
             "tt_tsqr_query", "tt_tsqr", "tt_small_svd_query", "tt_small_svd", "tt_tsmm",
             "tt_gen_uniform", "tt_batched_query", "tt_svd_batched", "tt_serve_create",
             "tt_serve_submit", "tt_serve_poll", "tt_serve_destroy", "tt_status_str",
-            "tt_profile", "tt_profile_read", "tt_stats", "tt_last_error", "tt_small_svd_noalloc", "tt_tune_set"]
+            "tt_profile", "tt_profile_read", "tt_stats", "tt_last_error", "tt_small_svd_noalloc", "tt_tune_set",
+            "tt_query_from_host", "tt_svd_from_host"]
 
 
 class tt_opts(C.Structure):
@@ -64,6 +65,11 @@ _SIGS = {
     "tt_svd_ex": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
                             C.c_void_p]),
+    "tt_query_from_host": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int,
+                                     C.c_void_p]),
+    "tt_svd_from_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                   C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
     "tt_last_device_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tt_tsqr_query": (C.c_int, [C.c_int64, C.c_int, C.c_int, C.c_void_p]),
     "tt_tsqr": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_int64, C.c_void_p, C.c_void_p,
@@ -149,6 +155,21 @@ def tt_svd(X_ptr, dt, d, n, r_max, tol, core_ptrs, ranks_ptr, sigma_ptr, err2_pt
                            sigma_ptr, err2_ptr, work_ptr, work_bytes, stream,
                            C.byref(opts) if opts is not None else None)
     check(code, "tt_svd")
+
+
+def tt_query_from_host(d, n, r_max, tol, dt, chunks=0):
+    wb = C.c_size_t(0)
+    check(lib().tt_query_from_host(d, i64_array(n), r_max, tol, dt, chunks, C.byref(wb)),
+          "tt_query_from_host")
+    return wb.value
+
+
+def tt_svd_from_host(Xh_ptr, Xd_ptr, dt, d, n, r_max, tol, chunks, core_ptrs, ranks_ptr, sigma_ptr,
+                     err2_ptr, work_ptr, work_bytes, stream=0, opts: tt_opts | None = None):
+    code = lib().tt_svd_from_host(Xh_ptr, Xd_ptr, dt, d, i64_array(n), r_max, tol, chunks,
+                                  ptr_array(core_ptrs), ranks_ptr, sigma_ptr, err2_ptr, work_ptr,
+                                  work_bytes, stream, C.byref(opts) if opts is not None else None)
+    check(code, "tt_svd_from_host")
 
 
 def tt_last_device_status(work_ptr, stream=0):

@@ -196,7 +196,7 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
 }
 
 static std::vector<TsqrLevel> plan_tsqr(int64_t rows, int m_max, Fmt in, Fmt comp1, Fmt comp2,
-                                        int nsm, int64_t ctas_override) {
+                                        int nsm, int64_t ctas_override, int chunks = 1) {
   std::vector<TsqrLevel> lv;
   Fmt cur = in;
   int64_t r = rows;
@@ -204,6 +204,25 @@ static std::vector<TsqrLevel> plan_tsqr(int64_t rows, int m_max, Fmt in, Fmt com
   for (int guard = 0; guard < 24; ++guard) {
     const Fmt comp = first ? comp1 : comp2;
     const Fmt out = comp;  // partial R's are stored in the arithmetic of their level
+    if (first && chunks > 1) {
+      // first level in row blocks (input streamed in): every block is launched on its own
+      // with the whole grid and writes its own partial R's
+      const int64_t crows = (rows + chunks - 1) / chunks;
+      TsqrLevel L = make_level(crows, m_max, cur, comp, out, true, nsm, ctas_override);
+      {
+        L.chunks = (int)((rows + crows - 1) / crows);
+        L.chunk_rows = crows;
+        L.chunk_parts = L.warps;
+        L.rows = rows;
+        L.warps = L.chunk_parts * L.chunks;
+        lv.push_back(L);
+        r = L.warps * L.mb;
+        cur = out;
+        first = false;
+        if (L.warps == 1) return lv;
+        continue;
+      }
+    }
     TsqrLevel L = make_level(r, m_max, cur, comp, out, first, nsm, ctas_override);
     lv.push_back(L);
     if (L.warps == 1) return lv;
@@ -234,6 +253,7 @@ struct Plan {
   int r_max;
   double tol;
   tt_dtype dt;
+  int in_chunks = 1;   // > 1: X arrives from the host in row blocks of the first active step
   Fmt xfmt, inter, comp_tsqr1, comp_tsqr2, comp_svd, comp_tsmm;
   std::vector<StepPlan> steps;
   int r_worst[TT_MAX_D + 1];
@@ -268,7 +288,7 @@ static tt_status validate(int d, const int64_t* n, int r_max, double tol) {
 }
 
 static tt_status build_plan(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
-                            const tt_opts* opts, Plan& P) {
+                            const tt_opts* opts, Plan& P, int in_chunks = 1) {
   tt_status st = validate(d, n, r_max, tol);
   if (st != TT_OK) return st;
   if (dt != TT_F64 && dt != TT_F32) return TT_EINVAL;
@@ -280,6 +300,7 @@ static tt_status build_plan(int d, const int64_t* n, int r_max, double tol, tt_d
   P.r_max = r_max;
   P.tol = tol;
   P.dt = dt;
+  P.in_chunks = std::max(1, in_chunks);
   if (dt == TT_F32) {
     P.xfmt = Fmt::F32; P.inter = Fmt::F32;
     P.comp_tsqr1 = Fmt::F32; P.comp_tsqr2 = Fmt::DF; P.comp_svd = Fmt::DF; P.comp_tsmm = Fmt::F32;
@@ -315,7 +336,9 @@ static tt_status build_plan(int d, const int64_t* n, int r_max, double tol, tt_d
     S.out_buf = -1;
     P.m_all_max = std::max(P.m_all_max, S.m_max);
     if (!S.elide) {
-      S.levels = plan_tsqr(rows, S.m_max, cur, P.comp_tsqr1, P.comp_tsqr2, nsm, ctas_override);
+      const bool first_active = P.szR == 0;  // no TSQR planned yet
+      S.levels = plan_tsqr(rows, S.m_max, cur, P.comp_tsqr1, P.comp_tsqr2, nsm, ctas_override,
+                           first_active ? P.in_chunks : 1);
       if (S.levels.empty()) return TT_ENOTIMPL;
       for (auto& L : S.levels) {
         P.szR = std::max(P.szR, (size_t)L.warps * L.mb * S.m_max * fmt_bytes(L.out));
@@ -377,9 +400,19 @@ static void sigma_layout(int d, const int64_t* n, const int* rw, int64_t* stride
   *count = s * std::max(d - 1, 0);
 }
 
+// row blocks of the first TSQR level when X is copied in from the host
+constexpr int kDefaultInChunks = 16;
+
+// X arriving from the host: the copy stream and one event per row block of the first level
+struct HostIn {
+  const char* X_host = nullptr;
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> ev;
+};
+
 static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out,
                           int64_t* ranks_out, double* sigma_out, double* err2_out, void* work,
-                          cudaStream_t s) {
+                          cudaStream_t s, HostIn* hin = nullptr) {
   char* wb = static_cast<char*>(work);
   DevState* st = reinterpret_cast<DevState*>(wb + P.off_state);
   int* status = &st->status;
@@ -387,6 +420,21 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
   int64_t sig_stride = 0, sig_count = 0;
   sigma_layout(d, P.n, P.r_worst, &sig_stride, &sig_count);
   TT_CK(launch_init_state(st, d, P.n, s));
+  if (hin && hin->X_host) {
+    // X is copied in row blocks by the first TSQR level when that level reads it;
+    // otherwise (every step elided) in one piece here
+    bool streamed = false;
+    for (const StepPlan& S : P.steps)
+      if (!S.elide) {
+        streamed = !S.levels.empty() && S.levels[0].chunks > 1;
+        break;
+      }
+    if (!streamed) {
+      size_t nb = fmt_bytes(P.xfmt);
+      for (int a = 0; a < d; ++a) nb *= (size_t)P.n[a];
+      TT_CK(cudaMemcpyAsync(const_cast<void*>(X), hin->X_host, nb, cudaMemcpyHostToDevice, s));
+    }
+  }
   ++g_launches;
   const void* cur = X;
   Fmt cur_fmt = P.xfmt;
@@ -416,7 +464,32 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
       const TsqrLevel& L = S.levels[l];
       void* Rout = wb + P.off_R[l & 1];
       const int64_t ldR = L.warps * L.mb;
-      {
+      if (L.chunks > 1) {
+        // first level in row blocks: block c (rows r0..r1 of every column) is copied from the
+        // host when X comes from there, and its launch waits only for that copy
+        prof::Scope ps(0, i, (double)L.rows * mm * fmt_bytes(L.in), 2.0 * (double)L.rows * mm * mm, s);
+        const size_t es = fmt_bytes(L.in);
+        for (int c = 0; c < L.chunks; ++c) {
+          const int64_t r0 = (int64_t)c * L.chunk_rows;
+          const int64_t r1 = std::min<int64_t>(L.rows, r0 + L.chunk_rows);
+          if (hin && hin->X_host && lin == X) {
+            TT_CK(cudaMemcpy2DAsync(static_cast<char*>(const_cast<void*>(X)) + r0 * es, lld * es,
+                                    hin->X_host + r0 * es, lld * es, (size_t)(r1 - r0) * es,
+                                    (size_t)S.m_max, cudaMemcpyHostToDevice, hin->cs));
+            TT_CK(cudaEventRecord(hin->ev[c], hin->cs));
+            TT_CK(cudaStreamWaitEvent(s, hin->ev[c], 0));
+          }
+          TsqrLevel Lc = L;
+          Lc.rows = r1 - r0;
+          Lc.panels = (Lc.rows + L.pr - 1) / L.pr;
+          Lc.chunks = 1;
+          Lc.warps = L.chunk_parts;
+          char* Rc = static_cast<char*>(Rout) + (size_t)c * L.chunk_parts * L.mb * fmt_bytes(L.out);
+          TT_CK(launch_tsqr_level(Lc, static_cast<const char*>(lin) + r0 * es, lld, &st->m[i], Rc,
+                                  ldR, wb + P.off_Rscr, status, s));
+          ++g_launches;
+        }
+      } else {
         prof::Scope ps(l == 0 ? 0 : 1, i, (double)L.rows * mm * fmt_bytes(L.in),
                        2.0 * (double)L.rows * mm * mm, s);
         TT_CK(launch_tsqr_level(L, lin, lld, &st->m[i], Rout, ldR, wb + P.off_Rscr, status, s));
@@ -589,6 +662,66 @@ tt_status tt_svd_ex(const void* X, tt_dtype dt, int d, const int64_t* n, int r_m
   if (st != TT_OK) return st;
   if (work_bytes < P.total) return TT_ENOMEM;
   return run_plan(P, X, cores_out, ranks_out, sigma_out, err2_out, work, (cudaStream_t)stream);
+}
+
+tt_status tt_query_from_host(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
+                             int chunks, size_t* work_bytes) {
+  if (chunks < 0 || chunks > 4096 || !work_bytes) return TT_EINVAL;
+  const int K = chunks ? chunks : kDefaultInChunks;
+  Plan P;
+  tt_status st = build_plan(d, n, r_max, tol, dt, nullptr, P, K);
+  if (st != TT_OK) return st;
+  size_t total = P.total;
+  for (int ne = 0; ne <= 1; ++ne)
+    for (int ar = (int)TT_ARITH_DF; ar <= (int)TT_ARITH_F64; ++ar) {
+      tt_opts o{};
+      o.arith = (tt_arith)ar;
+      o.no_elide = ne;
+      Plan Q;
+      if (build_plan(d, n, r_max, tol, dt, &o, Q, K) == TT_OK) total = std::max(total, Q.total);
+    }
+  *work_bytes = total;
+  return TT_OK;
+}
+
+tt_status tt_svd_from_host(const void* X_host, void* X_dev, tt_dtype dt, int d, const int64_t* n,
+                           int r_max, double tol, int chunks, double* const* cores_out,
+                           int64_t* ranks_out, double* sigma_out, double* err2_out, void* work,
+                           size_t work_bytes, void* stream, const tt_opts* opts) {
+  if (!X_host || !X_dev || !cores_out || !work || chunks < 0 || chunks > 4096) return TT_EINVAL;
+  for (int i = 0; i < d && i < TT_MAX_D; ++i)
+    if (!cores_out[i]) return TT_EINVAL;
+  if (((uintptr_t)work & 255) != 0) return TT_EINVAL;
+  Plan P;
+  tt_status st = build_plan(d, n, r_max, tol, dt, opts, P, chunks ? chunks : kDefaultInChunks);
+  if (st != TT_OK) return st;
+  if (work_bytes < P.total) return TT_ENOMEM;
+  const cudaStream_t s = (cudaStream_t)stream;
+  int nev = 0;
+  for (const StepPlan& S : P.steps)
+    if (!S.elide) {
+      nev = S.levels.empty() ? 0 : S.levels[0].chunks;
+      break;
+    }
+  HostIn hin;
+  hin.X_host = static_cast<const char*>(X_host);
+  // the copy stream forks from `stream` (so it also follows earlier work that reads X_dev)
+  // and joins it through the per-block events; stream and events are released when done
+  cudaEvent_t fork = nullptr;
+  tt_status ret = TT_OK;
+  if (cuda_err(cudaStreamCreateWithFlags(&hin.cs, cudaStreamNonBlocking)) != TT_OK) return TT_ECUDA;
+  hin.ev.assign(std::max(nev, 0), nullptr);
+  bool ok = cuda_err(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) == TT_OK;
+  for (auto& e : hin.ev)
+    ok = ok && cuda_err(cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) == TT_OK;
+  ok = ok && cuda_err(cudaEventRecord(fork, s)) == TT_OK;
+  ok = ok && cuda_err(cudaStreamWaitEvent(hin.cs, fork, 0)) == TT_OK;
+  ret = ok ? run_plan(P, X_dev, cores_out, ranks_out, sigma_out, err2_out, work, s, &hin) : TT_ECUDA;
+  for (auto& e : hin.ev)
+    if (e) cudaEventDestroy(e);
+  if (fork) cudaEventDestroy(fork);
+  cudaStreamDestroy(hin.cs);
+  return ret;
 }
 
 tt_status tt_svd(const void* X, tt_dtype dt, int d, const int64_t* n, int r_max, double tol,

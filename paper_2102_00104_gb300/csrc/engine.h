@@ -57,6 +57,9 @@ struct TsqrLevel {
   int64_t panels;
   size_t smem;       // dynamic smem per CTA
   Fmt in, comp, out;
+  int chunks = 1;            // first level only: launched once per row block of chunk_rows
+  int64_t chunk_rows = 0;    // rows with the full grid; each block writes chunk_parts partial
+  int64_t chunk_parts = 0;   // R's, so warps = chunks * chunk_parts
 };
 
 cudaError_t launch_tsqr_level(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,

@@ -132,3 +132,23 @@ def test_batched_and_serve_argument_checks(lib):
     res = capi.tt_job_result()
     assert lib.tt_serve_poll(None, 1, 0, C.byref(res)) == capi.TT_EINVAL
     assert lib.tt_serve_destroy(None) == capi.TT_EINVAL
+
+
+def test_from_host_argument_checks(lib):
+    n = capi.i64_array([4, 5, 6])
+    wb = C.c_size_t(0)
+    assert lib.tt_query_from_host(3, n, 3, 0.0, capi.TT_F64, -1, C.byref(wb)) == capi.TT_EINVAL
+    assert lib.tt_query_from_host(3, n, 3, 0.0, capi.TT_F64, 0, None) == capi.TT_EINVAL
+    assert lib.tt_query_from_host(3, n, 3, 0.0, capi.TT_F64, 0, C.byref(wb)) == capi.TT_OK
+    # the streamed plan keeps the partial R's of every row block: never smaller than tt_query's
+    assert wb.value >= capi.tt_query(3, [4, 5, 6], 3, 0.0, capi.TT_F64)[1]
+    cores = capi.ptr_array([4096, 4096, 4096])
+    args = (capi.TT_F64, 3, n, 3, 0.0, 0, cores, None, None, None, C.c_void_p(4096), 1 << 20, None, None)
+    assert lib.tt_svd_from_host(None, C.c_void_p(4096), *args) == capi.TT_EINVAL
+    assert lib.tt_svd_from_host(C.c_void_p(4096), None, *args) == capi.TT_EINVAL
+    bad_chunks = list(args)
+    bad_chunks[5] = 5000
+    assert lib.tt_svd_from_host(C.c_void_p(4096), C.c_void_p(4096), *bad_chunks) == capi.TT_EINVAL
+    misaligned = list(args)
+    misaligned[10] = C.c_void_p(4097)
+    assert lib.tt_svd_from_host(C.c_void_p(4096), C.c_void_p(4096), *misaligned) == capi.TT_EINVAL

@@ -134,3 +134,39 @@ def test_repeated_runs_are_identical():
     assert a.ranks == b.ranks
     for ca, cb in zip(a.cores, b.cores):
         assert torch.equal(ca, cb)
+
+
+# X in pinned host memory, copied in row blocks that overlap the first TSQR level
+HOST_CASES = [((4,) * 10, 8, 0), ((8, 8, 8, 8, 8), 10, 5), ((2,) * 12, 5, 3), ((5, 6, 7), 100, 0),
+              ((17, 3, 11), 5, 4), ((4, 4, 4, 4, 4), 1, 7), ((8,) * 6, 4, 1), ((3, 4, 5, 6, 7), 3, 64)]
+
+
+@pytest.mark.parametrize("dims,r_max,chunks", HOST_CASES)
+def test_from_host_parity(dims, r_max, chunks):
+    X = uniform_tensor(dims, seed=11)
+    plan = api.TTSVDPlan(dims, r_max, 0.0, torch.float64, "df", want_sigma=True)
+    Xh = fortran_flat(X).cpu().pin_memory()
+    plan.run_host(Xh, chunks=chunks)
+    res = plan.result()
+    # X arrived intact, and the result meets the same bar as the device-input call
+    assert torch.equal(plan.X_dev.cpu(), Xh)
+    compare(X, res, O.tt_svd(X, r_max), 1e-10)
+
+
+def test_from_host_fp32_and_repeat():
+    dims, r_max = (8, 8, 8, 8, 8), 16
+    X64 = uniform_tensor(dims, seed=12)
+    X32 = X64.astype(np.float32).astype(np.float64)
+    plan = api.TTSVDPlan(dims, r_max, 0.0, torch.float32, "df", want_sigma=True)
+    Xh = fortran_flat(X32, torch.float32).cpu().pin_memory()
+    plan.run_host(Xh, chunks=6)
+    a = plan.result()
+    compare(X32, a, O.tt_svd(X32, r_max), 1e-5)
+    # a second call on a new input reuses X_dev only after the first call has read it
+    Xh2 = fortran_flat(uniform_tensor(dims, seed=13).astype(np.float32).astype(np.float64),
+                       torch.float32).cpu().pin_memory()
+    plan.run_host(Xh, chunks=6)
+    plan.run_host(Xh2, chunks=6)
+    b = plan.result()
+    X2 = uniform_tensor(dims, seed=13).astype(np.float32).astype(np.float64)
+    compare(X2, b, O.tt_svd(X2, r_max), 1e-5)
