@@ -59,6 +59,9 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip sweep, FP32 form, e2e, CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--serve-seconds", type=float, default=4.0)
+    p.add_argument("--case", default="", help="one building block for profiling instead of the bench: "
+                   "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix) or svd:M "
+                   "(small SVD of a uniform upper-triangular R); prints one JSON line")
     return p.parse_args()
 
 
@@ -190,10 +193,54 @@ def lookup_traffic(kernel: str, workload: str):
     return e.get("bytes_per_launch")
 
 
+def run_case(spec: str) -> int:
+    """One building block, warmed up and run three times (for ncu captures of one kernel)."""
+    import torch
+
+    import __graft_entry__ as G
+    from paper_2102_00104_gb300 import api, capi
+
+    G.build()
+    capi.lib()
+    parts = spec.split(":")
+    s = torch.cuda.current_stream()
+    if parts[0] == "tsqr":
+        rows, m = int(parts[1]), int(parts[2])
+        if len(parts) > 3:
+            bucket = 0 if m <= 32 else 1 if m <= 64 else 2 if m <= 80 else 3 if m <= 128 else 4
+            capi.tt_tune_set(f"tsqr.colcfg.{bucket}", int(parts[3]))
+        W = api.gen_uniform(rows * m, 3, torch.float64)
+        R = torch.empty(m * m, dtype=torch.float64, device="cuda")
+        wb = capi.tt_tsqr_query(rows, m, capi.TT_F64)
+        work = torch.empty(wb + 256, dtype=torch.uint8, device="cuda")
+        wp = (work.data_ptr() + 255) & ~255
+        call = lambda: capi.tt_tsqr(W.data_ptr(), capi.TT_F64, rows, m, rows, R.data_ptr(), wp, wb,
+                                    int(s.cuda_stream))
+    elif parts[0] == "svd":
+        m = int(parts[1])
+        g = torch.Generator(device="cuda").manual_seed(0)
+        Rm = torch.triu(torch.rand(m, m, dtype=torch.float64, device="cuda", generator=g)).contiguous()
+        call = lambda: api.small_svd(Rm)
+    else:
+        raise SystemExit(f"unknown case {spec}")
+    call()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(3):
+        call()
+    b.record(s)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": spec, "ms": a.elapsed_time(b) / 3}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args.case)
 
     import torch
     import torch.distributed as dist
