@@ -120,6 +120,10 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
   int cta_kind = 3;
   int cta_cfg = m_max > 16 ? tsqr_col_pick(m_max, in, comp, out, &cta_pr, &cta_nw, &cta_per_sm) : -1;
   if (cta_cfg < 0) {
+    cta_kind = 4;
+    cta_cfg = tsqr_cols_pick(m_max, in, comp, out, &cta_pr, &cta_nw, &cta_per_sm);
+  }
+  if (cta_cfg < 0) {
     cta_kind = 2;
     cta_cfg = m_max > 16 ? tsqr_cta_pick(m_max, comp, &cta_pr, &cta_nw, &cta_per_sm) : -1;
   }
@@ -130,7 +134,9 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
     L.maxm = m_max;
     L.pr = cta_pr;
     L.nw = cta_nw;
-    L.smem = cta_kind == 3 ? tsqr_col_smem(m_max, comp, cta_cfg) : tsqr_cta_smem(m_max, comp, cta_cfg);
+    L.smem = cta_kind == 3   ? tsqr_col_smem(m_max, comp, cta_cfg)
+             : cta_kind == 4 ? tsqr_cols_smem(m_max, cta_cfg)
+                             : tsqr_cta_smem(m_max, comp, cta_cfg);
     L.panels = (rows + L.pr - 1) / L.pr;
     int64_t ctas;
     if (first) {

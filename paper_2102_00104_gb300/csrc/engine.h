@@ -43,7 +43,8 @@ constexpr int kMaxM = 512;     // widest unfolding handled
 struct TsqrLevel {
   int kind;          // 0 = narrow (warp, register panels), 1 = wide (warp, smem panels),
                      // 2 = CTA-cooperative (register panels, R in shared memory),
-                     // 3 = column-owned CTA kernel (one barrier per column, look-ahead)
+                     // 3 = column-owned CTA kernel (one barrier per column, look-ahead),
+                     // 4 = column-owned with the panel in shared memory (wide m)
   int cfg;           // kind 2: layout id (see tsqr_cta.cu); kind 3: see tsqr_col.cu
   int maxm;          // narrow: 4/8/16 ; wide: 32*chunks (template bound)
   int mmax;          // worst-case m of this level (<= maxm)
@@ -75,6 +76,12 @@ int tsqr_col_pick(int m_max, Fmt in, Fmt comp, Fmt out, int* pr, int* nw, int* p
 size_t tsqr_col_smem(int m_max, Fmt comp, int id);
 cudaError_t launch_tsqr_col(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
                             void* Rout, int64_t ldR, int* status, cudaStream_t s);
+// kind 4 (shared-memory panels, R in an L2-resident global slice per CTA): rows per lane or -1
+int tsqr_cols_pick(int m_max, Fmt in, Fmt comp, Fmt out, int* pr, int* nw, int* per_sm);
+size_t tsqr_cols_smem(int m_max, int prl);
+size_t tsqr_cols_scratch(int m_max, int64_t ctas);
+cudaError_t launch_tsqr_cols(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
+                             void* Rout, int64_t ldR, void* Rscr, int* status, cudaStream_t s);
 cudaError_t launch_tsqr_cta(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
                             void* Rout, int64_t ldR, void* Rscr, int* status, cudaStream_t s);
 

@@ -147,11 +147,10 @@ __device__ __forceinline__ C dot_rows(const C (&x)[PRL], const C (&y)[PRL]) {
 // earlier reflectors of this panel) and R_{jn,jn}; publishes x, the pivot entry
 // R_jj - alpha and 1/t as pivot number g (slot g & 1) and stores R_{jn,jn} = alpha.
 template <int PRL, class C>
-__device__ __forceinline__ bool publish(const C (&x)[PRL], int jn, uint32_t g, C* R, int mstr,
-                                        C* slots, const Sync& S, int lane, C eps) {
+__device__ __forceinline__ bool publish_r(const C (&x)[PRL], C rjj, int jn, uint32_t g, C* R,
+                                          int mstr, C* slots, const Sync& S, int lane, C eps) {
   constexpr int PR = 32 * PRL;
   const int rn = prow(jn, mstr);
-  const C rjj = R[rn];
   const C D = warp_allsum(dot_rows<PRL>(x, x));
   C t = add(fmac(rjj, rjj, D), eps);
   C alpha = sqrt_(add(t, eps));
@@ -174,6 +173,11 @@ __device__ __forceinline__ bool publish(const C (&x)[PRL], int jn, uint32_t g, C
   __syncwarp();
   if (lane == 0) mbar_arrive(&S.full[sl]);
   return true;
+}
+template <int PRL, class C>
+__device__ __forceinline__ bool publish(const C (&x)[PRL], int jn, uint32_t g, C* R, int mstr,
+                                        C* slots, const Sync& S, int lane, C eps) {
+  return publish_r<PRL>(x, R[prow(jn, mstr)], jn, g, R, mstr, slots, S, lane, eps);
 }
 
 // One column step j = JB * NW + jj for warp w; pivot j is pivot number g.
