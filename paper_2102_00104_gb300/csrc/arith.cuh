@@ -74,19 +74,31 @@ __device__ __forceinline__ df dfdiv(df a, df b) {
   return add(q, mkdf(q3, 0.f));
 }
 __device__ __forceinline__ df div_(df a, df b) { return dfdiv(a, b); }
-// 1/b: FP32 reciprocal and one Newton step in df (relative error ~ (2^-23)^2)
+// hardware approximations (PTX rcp.approx / sqrt.approx, relative error about one ulp);
+// every use below is followed by a Newton step in float-float
+__device__ __forceinline__ float rcp_seed(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_seed(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// 1/b: FP32 reciprocal seed and one Newton step in df (relative error ~ (2^-23)^2)
 __device__ __forceinline__ df rcp_(df b) {
-  const float r0 = __frcp_rn(b.hi);
+  const float r0 = rcp_seed(b.hi);
   const df e = fnmac(b, mkdf(r0, 0.f), mkdf(1.f, 0.f));   // 1 - b r0
   return fmac(mkdf(r0, 0.f), e, mkdf(r0, 0.f));           // r0 + r0 e
 }
 __device__ __forceinline__ df sqrt_(df a) {
   // one Newton correction of the FP32 root: x + (a - x^2) / (2x), residual in df
   if (!(a.hi > 0.f)) return mkdf(0.f, 0.f);
-  float x = __fsqrt_rn(a.hi);
+  float x = sqrt_seed(a.hi);
   float p, e; eft_two_prod(x, x, p, e);
   df res = sub(a, mkdf(p, e));
-  float corr = __fdiv_rn(res.hi, __fmul_rn(2.f, x));
+  float corr = __fmul_rn(res.hi, rcp_seed(__fmul_rn(2.f, x)));
   return df_norm(x, corr);
 }
 __device__ __forceinline__ bool is_pos(df a) { return a.hi > 0.f; }
