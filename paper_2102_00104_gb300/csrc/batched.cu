@@ -52,7 +52,7 @@ double now_s() {
 }
 
 // ---- the pool of streams used by tt_svd_batched -----------------------------------
-constexpr int kPoolStreams = 16;
+constexpr int kPoolStreams = 32;
 struct StreamPool {
   int dev = -1;
   cudaStream_t s[kPoolStreams];
@@ -119,18 +119,25 @@ tt_status tt_svd_batched(int batch, const tt_job* jobs, void* work, size_t work_
   StreamPool* P = nullptr;
   if (get_pool(&P) != cudaSuccess) return TT_ECUDA;
   cudaStream_t cs = (cudaStream_t)stream;
-  // largest jobs first, dealt round-robin over the pool's streams
+  // longest jobs first, each onto the stream with the least estimated work so far
+  // (greedy LPT on a rough per-job time from the plan)
+  std::vector<double> cost(batch);
+  for (int i = 0; i < batch; ++i)
+    cost[i] = job_cost_estimate(jobs[i].d, jobs[i].n, jobs[i].r_max, jobs[i].tol, (int)jobs[i].dtype);
   std::vector<int> order(batch);
   for (int i = 0; i < batch; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wb[a] > wb[b]; });
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   const int ns = std::min(batch, kPoolStreams);
+  std::vector<double> load(ns, 0.0);
   if (cudaEventRecord(P->fork, cs) != cudaSuccess) return TT_ECUDA;
   for (int k = 0; k < ns; ++k)
     if (cudaStreamWaitEvent(P->s[k], P->fork, 0) != cudaSuccess) return TT_ECUDA;
   tt_status result = TT_OK;
   for (int t = 0; t < batch; ++t) {
     const int i = order[t];
-    tt_status st = run_job(jobs[i], static_cast<char*>(work) + off[i], wb[i], P->s[t % ns]);
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[k] += cost[i];
+    tt_status st = run_job(jobs[i], static_cast<char*>(work) + off[i], wb[i], P->s[k]);
     if (st != TT_OK && result == TT_OK) result = st;
   }
   for (int k = 0; k < ns; ++k) {

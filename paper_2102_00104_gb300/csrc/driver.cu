@@ -670,6 +670,26 @@ tt_status tt_svd_ex(const void* X, tt_dtype dt, int d, const int64_t* n, int r_m
   return run_plan(P, X, cores_out, ranks_out, sigma_out, err2_out, work, (cudaStream_t)stream);
 }
 
+}  // extern "C"
+
+namespace tt {
+// Rough device time of one tt_svd (seconds) for scheduling batches: float-float TSQR at
+// ~2 TFLOP/s, one-sided Jacobi ~10 sweeps of m rounds at ~1.5 us, W*V_r at ~2 TFLOP/s.
+double job_cost_estimate(int d, const int64_t* n, int r_max, double tol, int dt) {
+  Plan P;
+  if (build_plan(d, n, r_max, tol, (tt_dtype)dt, nullptr, P) != TT_OK) return 0.0;
+  double t = 0.0;
+  for (const StepPlan& S : P.steps) {
+    if (S.elide) continue;
+    const double m = S.m_max, rows = (double)S.rows;
+    t += 2.0 * rows * m * m / 2e12 + 10.0 * m * 1.5e-6 + 2.0 * rows * m * S.r_max_out / 2e12 + 20e-6;
+  }
+  return t;
+}
+}  // namespace tt
+
+extern "C" {
+
 tt_status tt_query_from_host(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
                              int chunks, size_t* work_bytes) {
   if (chunks < 0 || chunks > 4096 || !work_bytes) return TT_EINVAL;

@@ -35,6 +35,9 @@ struct DevState {
 
 constexpr int kMaxM = 512;     // widest unfolding handled
 
+// rough device time (s) of one tt_svd with these arguments, for batch scheduling
+double job_cost_estimate(int d, const int64_t* n, int r_max, double tol, int dt);
+
 // ---- TSQR ---------------------------------------------------------------------
 // One TSQR level: every warp runs a flat tree of Alg. 6 panels over its share of
 // the rows of W (rows x m, leading dimension ld, format in) and writes its R
