@@ -81,7 +81,7 @@ def test_tsqr_rank_deficient_and_zero_columns():
     assert np.all(np.isfinite(Z)) and np.max(np.abs(Z)) < 1e-15
 
 
-@pytest.mark.parametrize("m,rank", [(64, 10), (80, 10), (128, 7), (32, 3)])
+@pytest.mark.parametrize("m,rank", [(64, 10), (80, 10), (128, 7), (32, 3), (200, 12), (400, 9)])
 def test_tsqr_low_rank_wide_panels(m, rank):
     # exactly low-rank W: after `rank` reflectors the panel columns hold only rounding
     # noise, which the float-float updates must keep at noise level (no growth, no NaN)
