@@ -22,6 +22,9 @@ Modules
                    and a LAPACK SVD of R; used to pin Alg. 1 == Alg. 2.
 ``model``          the performance model of Sec. 4 (Eqs. for TSQR/TSMM flops
                    and bytes, Eq. TT-SVD_data_volume, Eq. TT-SVD_operations).
+``thick_bounds``   Alg. 3 (thick-bounds TT-SVD, Sec. 3.1.3): combined right-most
+                   dimensions, TT-SVD of the reshaped tensor, recovery of the
+                   combined cores from a TT-SVD of the last core.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, library routines, brute force or values printed in the
