@@ -396,6 +396,22 @@ def run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, 
         del Xh
     except Exception as e:  # pinned 8 GiB may be refused on small hosts
         out["e2e"] = {"value": None, "unit": "GB/s", "error": str(e)[:200]}
+    # thick-bounds variant (Alg. 3, m_min = 16, f1_min = 1/2) beside the plain algorithm
+    thick = {}
+    for r in (1, 5, 10):
+        p = api.TTSVDPlan(dims, r, 0.0, torch.float64, args.arith, thick=(16, 0.5))
+        p.run(X)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(2):
+            p.run(X)
+        b.record(stream)
+        torch.cuda.synchronize()
+        res = p.result()
+        thick[str(r)] = {"ms": a.elapsed_time(b) / 2, "ranks": res.ranks}
+        del p
+    out["thick_bounds_fp64"] = thick
     # r_max sweep (outside the timed region)
     sweep = {}
     for r in (1, 5, 10, 20, 50):

@@ -69,6 +69,19 @@ typedef struct {
   tt_arith arith;      /* see tt_arith */
   int no_elide;        /* 1: run every step even when V would be square (see tt_svd) */
   int tsqr_ctas;       /* 0 = auto; else number of CTAs of the first TSQR level */
+  /* Thick-bounds variant (Alg. 3, Sec. 3.1.3), off when thick_m_min = 0: the k
+   * right-most dimensions are combined, with k the smallest count such that
+   * m = n_{d-k+1}...n_d >= max(thick_m_min, r_est / thick_f1_min) (r_est =
+   * thick_r_est, or r_max when 0); the reshaped tensor is decomposed by Alg. 2
+   * and the cores of the combined dimensions are recovered by Alg. 2 applied to
+   * the last core T_bar reshaped to (r, n_{d-k+1}, ..., n_d), whose first core
+   * is absorbed into the core to its left.  Only tol = 0 (TT_ENOTIMPL
+   * otherwise); sigma_out must be NULL; err2_out receives the reduced
+   * decomposition's discarded sigma^2 plus the recovery's (the latter relative
+   * to the orthonormal T_bar).  k <= 1 or k = d is the plain algorithm. */
+  int thick_m_min;
+  double thick_f1_min; /* > 0; 0.5 when 0 */
+  int thick_r_est;
 } tt_opts;
 
 /* ---- sizing ---------------------------------------------------------------
@@ -79,6 +92,11 @@ typedef struct {
  * r_max < 1 or tol < 0. */
 tt_status tt_query(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
                    size_t* core_bytes, size_t* work_bytes);
+
+/* tt_query for the given options (opts may be NULL): the thick-bounds variant
+ * needs the workspaces of both of its decompositions. */
+tt_status tt_query_ex(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
+                      const tt_opts* opts, size_t* core_bytes, size_t* work_bytes);
 
 /* Worst-case element count of each core (host array caps[d]) and of the
  * sigma_out buffer (*sigma_count): sigma_out holds, for step i = d..2 in that

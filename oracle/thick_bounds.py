@@ -34,6 +34,12 @@ class ThickResult:
     recovery: TTResult | None = None  # TT-SVD of T_bar (line 4)
     notes: dict = field(default_factory=dict)
 
+    @property
+    def err2(self) -> float:
+        """Discarded sigma^2 of the reduced decomposition plus that of the recovery (the
+        latter measured on the orthonormal T_bar, so it is not scaled by X)."""
+        return float(self.reduced.err2 + (self.recovery.err2 if self.recovery else 0.0))
+
 
 def tt_svd_thick(X: np.ndarray, r_max: int, m_min: int = 16, f1_min: float = 0.5,
                  r_est: int | None = None) -> ThickResult:

@@ -45,15 +45,20 @@ class TTSVDPlan:
     """
 
     def __init__(self, dims, r_max: int, tol: float = 0.0, dtype=torch.float64, arith: str = "df",
-                 want_sigma: bool = False, no_elide: bool = False, device="cuda", tsqr_ctas: int = 0):
+                 want_sigma: bool = False, no_elide: bool = False, device="cuda", tsqr_ctas: int = 0,
+                 thick=None):
+        """thick = (m_min, f1_min[, r_est]) selects the thick-bounds variant (Alg. 3)."""
         self.dims = [int(x) for x in dims]
         self.d = len(self.dims)
         self.r_max = int(r_max)
         self.tol = float(tol)
         self.dtype = dtype
         self.dt = _DT[dtype]
-        self.opts = capi.tt_opts(_ARITH[arith], 1 if no_elide else 0, int(tsqr_ctas))
-        _, self.work_bytes = capi.tt_query(self.d, self.dims, self.r_max, self.tol, self.dt)
+        th = tuple(thick) if thick else (0, 0.0, 0)
+        th = th + (0,) * (3 - len(th))
+        self.opts = capi.tt_opts(_ARITH[arith], 1 if no_elide else 0, int(tsqr_ctas), int(th[0]),
+                                 float(th[1]), int(th[2]))
+        _, self.work_bytes = capi.tt_query_ex(self.d, self.dims, self.r_max, self.tol, self.dt, self.opts)
         # also large enough for run_host (first TSQR level in row blocks)
         self.work_bytes = max(self.work_bytes, capi.tt_query_from_host(
             self.d, self.dims, self.r_max, self.tol, self.dt, 0))

@@ -26,11 +26,12 @@ EXPORTED = ["tt_query", "tt_core_caps", "tt_svd", "tt_svd_ex", "tt_last_device_s
             "tt_gen_uniform", "tt_batched_query", "tt_svd_batched", "tt_serve_create",
             "tt_serve_submit", "tt_serve_poll", "tt_serve_destroy", "tt_status_str",
             "tt_profile", "tt_profile_read", "tt_stats", "tt_last_error", "tt_small_svd_noalloc", "tt_tune_set",
-            "tt_query_from_host", "tt_svd_from_host"]
+            "tt_query_from_host", "tt_svd_from_host", "tt_query_ex"]
 
 
 class tt_opts(C.Structure):
-    _fields_ = [("arith", C.c_int), ("no_elide", C.c_int), ("tsqr_ctas", C.c_int)]
+    _fields_ = [("arith", C.c_int), ("no_elide", C.c_int), ("tsqr_ctas", C.c_int),
+                ("thick_m_min", C.c_int), ("thick_f1_min", C.c_double), ("thick_r_est", C.c_int)]
 
 
 class tt_job(C.Structure):
@@ -65,6 +66,8 @@ _SIGS = {
     "tt_svd_ex": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
                             C.c_void_p]),
+    "tt_query_ex": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                              C.c_void_p]),
     "tt_query_from_host": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int,
                                      C.c_void_p]),
     "tt_svd_from_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
@@ -139,6 +142,13 @@ def ptr_array(ptrs):
 def tt_query(d, n, r_max, tol, dt):
     cb, wb = C.c_size_t(0), C.c_size_t(0)
     check(lib().tt_query(d, i64_array(n), r_max, tol, dt, C.byref(cb), C.byref(wb)), "tt_query")
+    return cb.value, wb.value
+
+
+def tt_query_ex(d, n, r_max, tol, dt, opts: tt_opts | None = None):
+    cb, wb = C.c_size_t(0), C.c_size_t(0)
+    check(lib().tt_query_ex(d, i64_array(n), r_max, tol, dt, C.byref(opts) if opts is not None else None,
+                            C.byref(cb), C.byref(wb)), "tt_query_ex")
     return cb.value, wb.value
 
 

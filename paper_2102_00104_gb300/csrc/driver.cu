@@ -378,6 +378,67 @@ static tt_status build_plan(int d, const int64_t* n, int r_max, double tol, tt_d
   return TT_OK;
 }
 
+// ---- thick-bounds variant (Alg. 3) -----------------------------------------------------
+// line 1: the smallest k with m = n_{d-k+1}...n_d >= max(m_min, r_est / f1_min)
+static int thick_k(int d, const int64_t* n, double m_min, double f1_min, double r_est) {
+  double m = 1;
+  for (int k = 1; k <= d; ++k) {
+    m *= (double)n[d - k];
+    if (m >= std::max(m_min, r_est / f1_min)) return k;
+  }
+  return d;
+}
+
+struct ThickPlan {
+  int k = 0, d1 = 0, d2 = 0;
+  int64_t n1[TT_MAX_D], n2[TT_MAX_D];
+  Plan P1, P2;
+  int a = 0, b = 0, r1 = 0, rho1 = 0;
+  size_t off_w1 = 0, off_w2 = 0, off_tbar = 0, off_s0 = 0, off_told = 0, off_r1 = 0, off_r2 = 0,
+         off_e = 0, total = 0;
+};
+
+// TT_OK with T.k >= 2: the thick plan; TT_OK with T.k < 2: the plain algorithm applies
+static tt_status build_thick(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
+                             const tt_opts* opts, ThickPlan& T) {
+  tt_status st = validate(d, n, r_max, tol);
+  if (st != TT_OK) return st;
+  const double f1 = opts->thick_f1_min > 0 ? opts->thick_f1_min : 0.5;
+  const double rest = opts->thick_r_est > 0 ? opts->thick_r_est : r_max;
+  const int k = thick_k(d, n, opts->thick_m_min, f1, rest);
+  T.k = k;
+  if (k <= 1 || k >= d) return TT_OK;
+  if (tol != 0.0) return TT_ENOTIMPL;
+  tt_opts o = *opts;
+  o.thick_m_min = 0;
+  T.d1 = d - k + 1;
+  T.d2 = k + 1;
+  int64_t m = 1;
+  for (int i = d - k; i < d; ++i) m *= n[i];
+  for (int i = 0; i < d - k; ++i) T.n1[i] = n[i];
+  T.n1[d - k] = m;
+  if ((st = build_plan(T.d1, T.n1, r_max, 0.0, dt, &o, T.P1)) != TT_OK) return st;
+  T.a = T.P1.r_worst[d - k - 1];
+  T.b = (int)n[d - k - 1];
+  T.r1 = T.P1.r_worst[d - k];
+  T.n2[0] = T.r1;
+  for (int i = 1; i <= k; ++i) T.n2[i] = n[d - k + i - 1];
+  // the recovery decomposes the FP64 core T_bar, whatever the storage of X
+  if ((st = build_plan(T.d2, T.n2, r_max, 0.0, TT_F64, &o, T.P2)) != TT_OK) return st;
+  T.rho1 = T.P2.r_worst[1];
+  size_t off = 0;
+  T.off_w1 = off; off += align256(T.P1.total);
+  T.off_w2 = off; off += align256(T.P2.total);
+  T.off_tbar = off; off += align256((size_t)T.r1 * m * sizeof(double));
+  T.off_s0 = off; off += align256((size_t)T.r1 * T.rho1 * sizeof(double));
+  T.off_told = off; off += align256((size_t)T.a * T.b * T.r1 * sizeof(double));
+  T.off_r1 = off; off += align256((size_t)(T.d1 + 1) * sizeof(int64_t));
+  T.off_r2 = off; off += align256((size_t)(T.d2 + 1) * sizeof(int64_t));
+  T.off_e = off; off += align256(2 * sizeof(double));
+  T.total = off;
+  return TT_OK;
+}
+
 // last CUDA failure seen by a tt_* call on this thread (tt_last_error)
 static thread_local char g_last_err[256] = "";
 static void note_err(cudaError_t e, const char* what, int line) {
@@ -545,6 +606,35 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
   return TT_OK;
 }
 
+// Alg. 3: lines 2-3 (reduced decomposition), line 4 (recovery of the combined cores and
+// absorption of the recovered first core), ranks and discarded energy of the joined train
+static tt_status run_thick(const ThickPlan& T, const void* X, double* const* cores_out,
+                           int64_t* ranks_out, double* err2_out, void* work, cudaStream_t s) {
+  char* wb = static_cast<char*>(work);
+  const int d = T.d1 + T.k - 1, k = T.k;
+  double* tbar = reinterpret_cast<double*>(wb + T.off_tbar);
+  double* s0 = reinterpret_cast<double*>(wb + T.off_s0);
+  double* told = reinterpret_cast<double*>(wb + T.off_told);
+  int64_t* r1 = reinterpret_cast<int64_t*>(wb + T.off_r1);
+  int64_t* r2 = reinterpret_cast<int64_t*>(wb + T.off_r2);
+  double* e = reinterpret_cast<double*>(wb + T.off_e);
+  double* c1[TT_MAX_D];
+  for (int i = 0; i < d - k; ++i) c1[i] = cores_out[i];
+  c1[d - k] = tbar;
+  tt_status st = run_plan(T.P1, X, c1, r1, nullptr, e, wb + T.off_w1, s);
+  if (st != TT_OK) return st;
+  double* c2[TT_MAX_D];
+  c2[0] = s0;
+  for (int i = 1; i <= k; ++i) c2[i] = cores_out[d - k + i - 1];
+  if ((st = run_plan(T.P2, tbar, c2, r2, nullptr, e + 1, wb + T.off_w2, s)) != TT_OK) return st;
+  double* left = cores_out[d - k - 1];
+  TT_CK(cudaMemcpyAsync(told, left, (size_t)T.a * T.b * T.r1 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TT_CK(launch_merge_core(told, s0, T.a * T.b, T.r1, T.rho1, left, s));
+  TT_CK(launch_join_ranks(r1, d - k, r2, k, ranks_out, e, err2_out, s));
+  g_launches += 2;
+  return TT_OK;
+}
+
 }  // namespace tt
 
 using namespace tt;
@@ -640,6 +730,16 @@ tt_status tt_query(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
   return TT_OK;
 }
 
+tt_status tt_query_ex(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
+                      const tt_opts* opts, size_t* core_bytes, size_t* work_bytes) {
+  tt_status st = tt_query(d, n, r_max, tol, dt, core_bytes, work_bytes);
+  if (st != TT_OK || !opts || opts->thick_m_min <= 0) return st;
+  ThickPlan T;
+  if ((st = build_thick(d, n, r_max, tol, dt, opts, T)) != TT_OK) return st;
+  if (T.k >= 2 && work_bytes) *work_bytes = std::max(*work_bytes, T.total);
+  return TT_OK;
+}
+
 tt_status tt_core_caps(int d, const int64_t* n, int r_max, int64_t* caps, int64_t* sigma_stride,
                        int64_t* sigma_count) {
   tt_status st = validate(d, n, r_max, 0.0);
@@ -663,6 +763,17 @@ tt_status tt_svd_ex(const void* X, tt_dtype dt, int d, const int64_t* n, int r_m
   for (int i = 0; i < d && i < TT_MAX_D; ++i)
     if (!cores_out[i]) return TT_EINVAL;
   if (((uintptr_t)work & 255) != 0) return TT_EINVAL;
+  if (opts && opts->thick_m_min > 0) {
+    if (opts->thick_m_min < 0 || opts->thick_f1_min < 0 || opts->thick_r_est < 0) return TT_EINVAL;
+    ThickPlan T;
+    tt_status st = build_thick(d, n, r_max, tol, dt, opts, T);
+    if (st != TT_OK) return st;
+    if (T.k >= 2) {
+      if (sigma_out) return TT_EINVAL;
+      if (work_bytes < T.total) return TT_ENOMEM;
+      return run_thick(T, X, cores_out, ranks_out, err2_out, work, (cudaStream_t)stream);
+    }
+  }
   Plan P;
   tt_status st = build_plan(d, n, r_max, tol, dt, opts, P);
   if (st != TT_OK) return st;

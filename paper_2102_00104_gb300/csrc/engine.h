@@ -119,6 +119,10 @@ cudaError_t launch_set_rank(DevState* st, int step_i, int n_next, int r, cudaStr
 // dst(i, k) = src(i, k) as FP64 for i < rows, k < cols (zero below the diagonal if upper)
 cudaError_t launch_copy_mat_f64(Fmt f, const void* src, int64_t lds, int rows, int cols, int upper,
                                 double* dst, int64_t ldd, cudaStream_t s);
+cudaError_t launch_merge_core(const double* Told, const double* S0, int ab, int r, int rho,
+                              double* Tnew, cudaStream_t s);
+cudaError_t launch_join_ranks(const int64_t* r1, int p, const int64_t* r2, int q, int64_t* out,
+                              const double* e12, double* err2_out, cudaStream_t s);
 cudaError_t launch_convert_to_f64(Fmt f, const void* src, int64_t count, double* dst,
                                   cudaStream_t s);
 cudaError_t launch_fill_nan(double* dst, int64_t count, cudaStream_t s);

@@ -236,6 +236,32 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
   }
 }
 
+// ---- thick-bounds recovery (Alg. 3 line 4) ------------------------------------------
+// T_new (ab x rho) = T_old (ab x r) * S0 (r x rho), column-major FP64: the recovered first
+// core S0 absorbed into the core to its left
+__global__ void k_merge_core(const double* __restrict__ Told, const double* __restrict__ S0,
+                             int ab, int r, int rho, double* __restrict__ Tnew) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)ab * rho;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % ab), c = (int)(idx / ab);
+    double acc = 0.0;
+    for (int t = 0; t < r; ++t) acc = fma(Told[i + (int64_t)t * ab], S0[t + (int64_t)c * r], acc);
+    Tnew[idx] = acc;
+  }
+}
+
+// ranks of the thick train: r_0..r_{p-1} of the reduced train, then rho_1..rho_{q+1} of the
+// recovery; err2 = the two discarded energies
+__global__ void k_join_ranks(const int64_t* r1, int p, const int64_t* r2, int q, int64_t* out,
+                             const double* e12, double* err2_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (out) {
+    for (int i = 0; i < p; ++i) out[i] = r1[i];
+    for (int i = 1; i <= q + 1; ++i) out[p + i - 1] = r2[i];
+  }
+  if (err2_out) *err2_out = e12[0] + e12[1];
+}
+
 // ---- rank choice: Alg. 2 lines 7-8 --------------------------------------------
 __global__ void k_truncate(const double* __restrict__ sigma, int64_t rows, int step_i, int n_next,
                            int r_max, double tol2_over_dm1, DevState* st,
@@ -486,6 +512,19 @@ cudaError_t launch_copy_mat_f64(Fmt f, const void* src, int64_t lds, int rows, i
 
 cudaError_t launch_core_identity(int m, double* core, cudaStream_t s) {
   k_core_identity<<<grid_for((int64_t)m * m, 256), 256, 0, s>>>(m, core);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_core(const double* Told, const double* S0, int ab, int r, int rho,
+                              double* Tnew, cudaStream_t s) {
+  const int64_t n = (int64_t)ab * rho;
+  k_merge_core<<<grid_for(n, 256), 256, 0, s>>>(Told, S0, ab, r, rho, Tnew);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_join_ranks(const int64_t* r1, int p, const int64_t* r2, int q, int64_t* out,
+                              const double* e12, double* err2_out, cudaStream_t s) {
+  k_join_ranks<<<1, 32, 0, s>>>(r1, p, r2, q, out, e12, err2_out);
   return cudaGetLastError();
 }
 

@@ -170,3 +170,30 @@ def test_from_host_fp32_and_repeat():
     b = plan.result()
     X2 = uniform_tensor(dims, seed=13).astype(np.float32).astype(np.float64)
     compare(X2, b, O.tt_svd(X2, r_max), 1e-5)
+
+
+# thick-bounds variant (Alg. 3): parity with the oracle's Alg. 3
+from oracle.thick_bounds import tt_svd_thick  # noqa: E402
+
+THICK_CASES = [((2,) * 12, 1, 16, 0.5), ((2,) * 12, 5, 16, 0.5), ((2,) * 12, 16, 16, 0.5),
+               ((4,) * 8, 6, 16, 0.5), ((3, 4, 2, 2, 2, 3), 4, 8, 0.5), ((8,) * 6, 10, 16, 0.5),
+               ((5, 6, 40), 3, 16, 0.5)]
+
+
+@pytest.mark.parametrize("dims,r_max,m_min,f1", THICK_CASES)
+def test_thick_bounds_parity(dims, r_max, m_min, f1):
+    X = uniform_tensor(dims, seed=21)
+    plan = api.TTSVDPlan(dims, r_max, 0.0, torch.float64, "df", thick=(m_min, f1))
+    plan.run(fortran_flat(X))
+    res = plan.result()
+    ref = tt_svd_thick(X, r_max, m_min, f1)
+    assert res.ranks == ref.ranks, (res.ranks, ref.ranks)
+    nx = np.linalg.norm(X)
+    cores = res.core_arrays()
+    err = np.linalg.norm(O.tt_full(cores) - X) / nx
+    err_ref = np.linalg.norm(O.tt_full(ref.cores) - X) / nx
+    assert abs(err - err_ref) <= 1e-10, (err, err_ref)
+    assert abs(res.err2 - ref.err2) <= 1e-10 * max(1.0, nx * nx)
+    d, k = len(dims), ref.k
+    for c in cores[d - k:] if k >= 2 else cores[1:]:
+        assert O.core_orthonormality_defect(c) <= 1e-12
