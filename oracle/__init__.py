@@ -25,6 +25,8 @@ Modules
 ``thick_bounds``   Alg. 3 (thick-bounds TT-SVD, Sec. 3.1.3): combined right-most
                    dimensions, TT-SVD of the reshaped tensor, recovery of the
                    combined cores from a TT-SVD of the last core.
+``two_sided``      Alg. 4 (two-sided TT-SVD, Sec. 3.1.3): cores alternately at the
+                   right and the left end, middle core last.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, library routines, brute force or values printed in the
