@@ -412,6 +412,22 @@ def run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, 
         thick[str(r)] = {"ms": a.elapsed_time(b) / 2, "ranks": res.ranks}
         del p
     out["thick_bounds_fp64"] = thick
+    # two-sided variant (Alg. 4)
+    two = {}
+    for r in (5, 10):
+        p = api.TTSVDPlan(dims, r, 0.0, torch.float64, args.arith, two_sided=True)
+        p.run(X)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(2):
+            p.run(X)
+        b.record(stream)
+        torch.cuda.synchronize()
+        res = p.result()
+        two[str(r)] = {"ms": a.elapsed_time(b) / 2, "ranks": res.ranks}
+        del p
+    out["two_sided_fp64"] = two
     # r_max sweep (outside the timed region)
     sweep = {}
     for r in (1, 5, 10, 20, 50):

@@ -82,6 +82,14 @@ typedef struct {
   int thick_m_min;
   double thick_f1_min; /* > 0; 0.5 when 0 */
   int thick_r_est;
+  /* 1: two-sided variant (Alg. 4, Sec. 3.1.3): cores alternately at the right and
+   * at the left end (i = d, 1, d-1, 2, ...), each by the TSQR + small SVD + W*V_r
+   * step; a left step works on the transposed left unfolding (an explicit
+   * transpose before and after it).  Core T^(i) of a left step has orthonormal
+   * columns in its (r_{i-1} n_i) x r_i matricization; the middle core carries the
+   * norm.  Only tol = 0 (TT_ENOTIMPL otherwise); sigma_out must be NULL; not
+   * combined with thick_m_min. */
+  int two_sided;
 } tt_opts;
 
 /* ---- sizing ---------------------------------------------------------------

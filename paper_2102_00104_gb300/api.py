@@ -46,8 +46,9 @@ class TTSVDPlan:
 
     def __init__(self, dims, r_max: int, tol: float = 0.0, dtype=torch.float64, arith: str = "df",
                  want_sigma: bool = False, no_elide: bool = False, device="cuda", tsqr_ctas: int = 0,
-                 thick=None):
-        """thick = (m_min, f1_min[, r_est]) selects the thick-bounds variant (Alg. 3)."""
+                 thick=None, two_sided: bool = False):
+        """thick = (m_min, f1_min[, r_est]) selects the thick-bounds variant (Alg. 3);
+        two_sided = True the two-sided variant (Alg. 4)."""
         self.dims = [int(x) for x in dims]
         self.d = len(self.dims)
         self.r_max = int(r_max)
@@ -57,7 +58,7 @@ class TTSVDPlan:
         th = tuple(thick) if thick else (0, 0.0, 0)
         th = th + (0,) * (3 - len(th))
         self.opts = capi.tt_opts(_ARITH[arith], 1 if no_elide else 0, int(tsqr_ctas), int(th[0]),
-                                 float(th[1]), int(th[2]))
+                                 float(th[1]), int(th[2]), 1 if two_sided else 0)
         _, self.work_bytes = capi.tt_query_ex(self.d, self.dims, self.r_max, self.tol, self.dt, self.opts)
         # also large enough for run_host (first TSQR level in row blocks)
         self.work_bytes = max(self.work_bytes, capi.tt_query_from_host(

@@ -31,7 +31,8 @@ EXPORTED = ["tt_query", "tt_core_caps", "tt_svd", "tt_svd_ex", "tt_last_device_s
 
 class tt_opts(C.Structure):
     _fields_ = [("arith", C.c_int), ("no_elide", C.c_int), ("tsqr_ctas", C.c_int),
-                ("thick_m_min", C.c_int), ("thick_f1_min", C.c_double), ("thick_r_est", C.c_int)]
+                ("thick_m_min", C.c_int), ("thick_f1_min", C.c_double), ("thick_r_est", C.c_int),
+                ("two_sided", C.c_int)]
 
 
 class tt_job(C.Structure):

@@ -439,6 +439,138 @@ static tt_status build_thick(int d, const int64_t* n, int r_max, double tol, tt_
   return TT_OK;
 }
 
+// ---- two-sided variant (Alg. 4) ------------------------------------------------------
+// The work tensor Z has the shape (r_L, n_a, ..., n_b, r_R) in Fortran order.  A right
+// step on b is the one-sided step; a left step on a transposes the (r_L n_a) x rest
+// unfolding, runs the same TSQR + SVD + W*V_r on it and transposes the product back.
+struct TsStep {
+  bool right = true, elide = false;
+  int dim = 0;          // 1-based dimension whose core the step writes
+  int64_t rows = 0;     // rows of the tall matrix of the step
+  int m = 0, r = 0;
+  Fmt in = Fmt::F64;    // format of Z before the step
+  std::vector<TsqrLevel> levels;
+  TsmmCfg tsmm{};
+  int zin = -1, zout = -1;  // Z buffers (-1: X)
+};
+
+struct TsPlan {
+  int d = 0, mid = 0, rl = 1, rr = 1;
+  int64_t n[TT_MAX_D];
+  int64_t ranks[TT_MAX_D + 1];
+  Fmt xfmt, inter, comp_tsqr1, comp_tsqr2, comp_svd, comp_tsmm;
+  std::vector<TsStep> steps;
+  int zfinal = -1;
+  Fmt zfmt_final = Fmt::F64;
+  int ldA = 2, m_all_max = 1;
+  size_t szZ[2] = {0, 0}, szT = 0, szY = 0, szR = 0, szRscr = 0, szJ = 0, szVout = 0;
+  size_t off_state = 0, off_Z[2] = {0, 0}, off_T = 0, off_Y = 0, off_R[2] = {0, 0}, off_Rscr = 0,
+         off_A = 0, off_V = 0, off_Vout = 0, off_sig = 0, off_e = 0, total = 0;
+};
+
+static tt_status build_two_sided(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
+                                 const tt_opts* opts, TsPlan& T) {
+  tt_status st = validate(d, n, r_max, tol);
+  if (st != TT_OK) return st;
+  if (dt != TT_F64 && dt != TT_F32) return TT_EINVAL;
+  if (tol != 0.0 || (opts && opts->thick_m_min > 0)) return TT_ENOTIMPL;
+  // the arithmetic of the one-sided plan
+  Plan P;
+  tt_opts o = opts ? *opts : tt_opts{};
+  o.two_sided = 0;
+  if ((st = build_plan(d, n, r_max, tol, dt, &o, P)) != TT_OK) return st;
+  T.d = d;
+  for (int i = 0; i < d; ++i) T.n[i] = n[i];
+  T.xfmt = P.xfmt; T.inter = P.inter; T.comp_tsqr1 = P.comp_tsqr1; T.comp_tsqr2 = P.comp_tsqr2;
+  T.comp_svd = P.comp_svd; T.comp_tsmm = P.comp_tsmm;
+  for (int i = 0; i <= d; ++i) T.ranks[i] = 1;
+  const int nsm = num_sms();
+  int a = 1, b = d, rL = 1, rR = 1, t = 0, zcur = -1;
+  Fmt cur = T.xfmt;
+  auto prod = [&](int lo, int hi) {  // n_lo ... n_hi (1-based, inclusive), 1 if empty
+    int64_t v = 1;
+    for (int i = lo; i <= hi; ++i) v *= n[i - 1];
+    return v;
+  };
+  while (a < b) {
+    TsStep S;
+    S.right = (t % 2 == 0);
+    S.in = cur;
+    S.zin = zcur;
+    if (S.right) {
+      S.dim = b;
+      S.rows = (int64_t)rL * prod(a, b - 1);
+      const int64_t m64 = n[b - 1] * (int64_t)rR;
+      if (m64 > kMaxM) return TT_ENOTIMPL;
+      S.m = (int)m64;
+      S.r = (int)std::min<int64_t>(r_max, std::min<int64_t>(S.rows, S.m));
+      S.elide = std::min<int64_t>(r_max, S.rows) >= S.m;
+    } else {
+      S.dim = a;
+      S.rows = prod(a + 1, b) * (int64_t)rR;
+      const int64_t m64 = (int64_t)rL * n[a - 1];
+      if (m64 > kMaxM) return TT_ENOTIMPL;
+      S.m = (int)m64;
+      S.r = (int)std::min<int64_t>(r_max, std::min<int64_t>(S.rows, S.m));
+      S.elide = std::min<int64_t>(r_max, S.rows) >= S.m;
+    }
+    T.m_all_max = std::max(T.m_all_max, S.m);
+    if (!S.elide) {
+      S.levels = plan_tsqr(S.rows, S.m, cur, T.comp_tsqr1, T.comp_tsqr2, nsm, 0);
+      if (S.levels.empty()) return TT_ENOTIMPL;
+      for (auto& L : S.levels) {
+        T.szR = std::max(T.szR, (size_t)L.warps * L.mb * S.m * fmt_bytes(L.out));
+        T.szRscr = std::max(T.szRscr, tsqr_wide_scratch_bytes(L));
+      }
+      S.tsmm = plan_tsmm(cur, T.comp_tsmm, T.comp_svd, T.inter, S.m, S.r, S.rows, nsm);
+      S.zout = zcur == 0 ? 1 : 0;
+      T.szZ[S.zout] = std::max(T.szZ[S.zout], (size_t)S.rows * S.r * fmt_bytes(T.inter));
+      if (!S.right) {
+        T.szT = std::max(T.szT, (size_t)S.rows * S.m * fmt_bytes(cur));
+        T.szY = std::max(T.szY, (size_t)S.rows * S.r * fmt_bytes(T.inter));
+      }
+      zcur = S.zout;
+      cur = T.inter;
+    }
+    if (S.right) {
+      T.ranks[b - 1] = S.r;
+      rR = S.r;
+      --b;
+    } else {
+      T.ranks[a] = S.r;
+      rL = S.r;
+      ++a;
+    }
+    T.steps.push_back(S);
+    ++t;
+  }
+  T.mid = a;
+  T.rl = rL;
+  T.rr = rR;
+  T.zfinal = zcur;
+  T.zfmt_final = cur;
+  const int mp = T.m_all_max + (T.m_all_max & 1);
+  T.ldA = mp;
+  T.szJ = jacobi_scratch_bytes(T.comp_svd, T.m_all_max);
+  T.szVout = (size_t)mp * mp * fmt_bytes(T.comp_svd);
+  size_t off = 0;
+  T.off_state = off; off += align256(sizeof(DevState));
+  T.off_Z[0] = off; off += align256(T.szZ[0]);
+  T.off_Z[1] = off; off += align256(T.szZ[1]);
+  T.off_T = off; off += align256(T.szT);
+  T.off_Y = off; off += align256(T.szY);
+  T.off_R[0] = off; off += align256(T.szR);
+  T.off_R[1] = off; off += align256(T.szR);
+  T.off_Rscr = off; off += align256(T.szRscr);
+  T.off_A = off; off += align256(T.szJ);
+  T.off_V = T.off_A + T.szJ / 2;
+  T.off_Vout = off; off += align256(T.szVout);
+  T.off_sig = off; off += align256((size_t)mp * sizeof(double));
+  T.off_e = off; off += align256(sizeof(double));
+  T.total = off;
+  return TT_OK;
+}
+
 // last CUDA failure seen by a tt_* call on this thread (tt_last_error)
 static thread_local char g_last_err[256] = "";
 static void note_err(cudaError_t e, const char* what, int line) {
@@ -606,6 +738,85 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
   return TT_OK;
 }
 
+// Alg. 4: the steps in the order d, 1, d-1, 2, ..., then the middle core
+static tt_status run_two_sided(const TsPlan& T, const void* X, double* const* cores_out,
+                               int64_t* ranks_out, double* err2_out, void* work, cudaStream_t s) {
+  char* wb = static_cast<char*>(work);
+  DevState* st = reinterpret_cast<DevState*>(wb + T.off_state);
+  int* status = &st->status;
+  double* e = reinterpret_cast<double*>(wb + T.off_e);
+  double* sig = reinterpret_cast<double*>(wb + T.off_sig);
+  void* Vout = wb + T.off_Vout;
+  TT_CK(launch_init_state(st, T.d, T.n, s));
+  TT_CK(launch_zero(e, s));
+  g_launches += 2;
+  auto zptr = [&](int z) -> const void* { return z < 0 ? X : (const void*)(wb + T.off_Z[z]); };
+  for (const TsStep& S : T.steps) {
+    double* core = cores_out[S.dim - 1];
+    if (S.elide) {
+      TT_CK(launch_core_identity(S.m, core, s));
+      ++g_launches;
+      continue;
+    }
+    const void* Z = zptr(S.zin);
+    const void* W = Z;
+    if (!S.right) {
+      // the tall matrix of a left step: the transpose of the (r_L n_a) x rest unfolding
+      TT_CK(launch_transpose(fmt_bytes(S.in), Z, S.m, S.rows, wb + T.off_T, s));
+      ++g_launches;
+      W = wb + T.off_T;
+    }
+    const void* lin = W;
+    int64_t lld = S.rows;
+    const void* Rfin = nullptr;
+    int64_t ldRfin = 0;
+    Fmt rfmt = Fmt::DF;
+    for (size_t l = 0; l < S.levels.size(); ++l) {
+      const TsqrLevel& L = S.levels[l];
+      void* Rout = wb + T.off_R[l & 1];
+      const int64_t ldR = L.warps * L.mb;
+      {
+        prof::Scope ps(l == 0 ? 0 : 1, S.dim, (double)L.rows * S.m * fmt_bytes(L.in),
+                       2.0 * (double)L.rows * S.m * S.m, s);
+        TT_CK(launch_tsqr_level(L, lin, lld, nullptr, Rout, ldR, wb + T.off_Rscr, status, s));
+        ++g_launches;
+      }
+      lin = Rout;
+      lld = ldR;
+      Rfin = Rout;
+      ldRfin = ldR;
+      rfmt = L.out;
+    }
+    {
+      prof::Scope ps(2, S.dim, 2.0 * S.m * S.m * fmt_bytes(T.comp_svd), 0.0, s);
+      TT_CK(launch_jacobi(T.comp_svd, rfmt, Rfin, ldRfin, nullptr, S.m, wb + T.off_A, wb + T.off_V,
+                          T.ldA, sig, Vout, T.ldA, status, nullptr, s));
+      ++g_launches;
+    }
+    TT_CK(launch_core_side(T.comp_svd, !S.right, Vout, T.ldA, S.m, S.r, core, s));
+    TT_CK(launch_add_discarded(sig, S.m, S.r, e, s));
+    g_launches += 2;
+    void* Zout = wb + T.off_Z[S.zout];
+    void* Y = S.right ? Zout : (void*)(wb + T.off_Y);
+    {
+      prof::Scope ps(4, S.dim, (double)S.rows * (S.m * fmt_bytes(S.in) + S.r * fmt_bytes(T.inter)),
+                     2.0 * (double)S.rows * S.m * S.r, s);
+      TT_CK(launch_tsmm(S.tsmm, W, S.rows, S.rows, nullptr, Vout, T.ldA, nullptr, Y, S.rows, status, s));
+      ++g_launches;
+    }
+    if (!S.right) {
+      // back to the (r, n_{a+1}, ..., r_R) layout of Z
+      TT_CK(launch_transpose(fmt_bytes(T.inter), Y, S.rows, S.r, Zout, s));
+      ++g_launches;
+    }
+  }
+  const int64_t cnt = (int64_t)T.rl * T.n[T.mid - 1] * T.rr;
+  TT_CK(launch_convert_to_f64(T.zfmt_final, zptr(T.zfinal), cnt, cores_out[T.mid - 1], s));
+  TT_CK(launch_put_ranks(T.ranks, T.d + 1, ranks_out, e, err2_out, s));
+  g_launches += 2;
+  return TT_OK;
+}
+
 // Alg. 3: lines 2-3 (reduced decomposition), line 4 (recovery of the combined cores and
 // absorption of the recovered first core), ranks and discarded energy of the joined train
 static tt_status run_thick(const ThickPlan& T, const void* X, double* const* cores_out,
@@ -733,7 +944,14 @@ tt_status tt_query(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
 tt_status tt_query_ex(int d, const int64_t* n, int r_max, double tol, tt_dtype dt,
                       const tt_opts* opts, size_t* core_bytes, size_t* work_bytes) {
   tt_status st = tt_query(d, n, r_max, tol, dt, core_bytes, work_bytes);
-  if (st != TT_OK || !opts || opts->thick_m_min <= 0) return st;
+  if (st != TT_OK || !opts) return st;
+  if (opts->two_sided) {
+    TsPlan T;
+    if ((st = build_two_sided(d, n, r_max, tol, dt, opts, T)) != TT_OK) return st;
+    if (work_bytes) *work_bytes = std::max(*work_bytes, T.total);
+    return TT_OK;
+  }
+  if (opts->thick_m_min <= 0) return st;
   ThickPlan T;
   if ((st = build_thick(d, n, r_max, tol, dt, opts, T)) != TT_OK) return st;
   if (T.k >= 2 && work_bytes) *work_bytes = std::max(*work_bytes, T.total);
@@ -763,6 +981,14 @@ tt_status tt_svd_ex(const void* X, tt_dtype dt, int d, const int64_t* n, int r_m
   for (int i = 0; i < d && i < TT_MAX_D; ++i)
     if (!cores_out[i]) return TT_EINVAL;
   if (((uintptr_t)work & 255) != 0) return TT_EINVAL;
+  if (opts && opts->two_sided) {
+    if (sigma_out) return TT_EINVAL;
+    TsPlan T;
+    tt_status st = build_two_sided(d, n, r_max, tol, dt, opts, T);
+    if (st != TT_OK) return st;
+    if (work_bytes < T.total) return TT_ENOMEM;
+    return run_two_sided(T, X, cores_out, ranks_out, err2_out, work, (cudaStream_t)stream);
+  }
   if (opts && opts->thick_m_min > 0) {
     if (opts->thick_m_min < 0 || opts->thick_f1_min < 0 || opts->thick_r_est < 0) return TT_EINVAL;
     ThickPlan T;

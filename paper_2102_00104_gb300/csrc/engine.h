@@ -123,6 +123,16 @@ cudaError_t launch_merge_core(const double* Told, const double* S0, int ab, int 
                               double* Tnew, cudaStream_t s);
 cudaError_t launch_join_ranks(const int64_t* r1, int p, const int64_t* r2, int q, int64_t* out,
                               const double* e12, double* err2_out, cudaStream_t s);
+// two-sided TT-SVD (two_sided.cu)
+constexpr int TT_MAX_RANKS = 40;
+cudaError_t launch_transpose(size_t elem, const void* in, int64_t P, int64_t Q, void* out,
+                             cudaStream_t s);
+cudaError_t launch_core_side(Fmt vfmt, bool left, const void* V, int ldV, int m, int r, double* core,
+                             cudaStream_t s);
+cudaError_t launch_add_discarded(const double* sigma, int cnt, int r, double* e, cudaStream_t s);
+cudaError_t launch_zero(double* e, cudaStream_t s);
+cudaError_t launch_put_ranks(const int64_t* ranks, int count, int64_t* ranks_out, const double* e,
+                             double* err2_out, cudaStream_t s);
 cudaError_t launch_convert_to_f64(Fmt f, const void* src, int64_t count, double* dst,
                                   cudaStream_t s);
 cudaError_t launch_fill_nan(double* dst, int64_t count, cudaStream_t s);

@@ -197,3 +197,47 @@ def test_thick_bounds_parity(dims, r_max, m_min, f1):
     d, k = len(dims), ref.k
     for c in cores[d - k:] if k >= 2 else cores[1:]:
         assert O.core_orthonormality_defect(c) <= 1e-12
+
+
+# two-sided variant (Alg. 4): parity with the oracle's Alg. 4
+from oracle.two_sided import tt_svd_two_sided  # noqa: E402
+
+TWO_SIDED_CASES = [((4,) * 7, 5), ((2,) * 12, 4), ((3, 4, 2, 5), 100), ((8,) * 6, 10), ((6, 5), 3),
+                   ((17, 3, 11, 4), 5), ((8,) * 5, 3)]
+
+
+def _left_defect(core):
+    r0, ni, r1 = core.shape
+    M = O.freshape(core, (r0 * ni, r1))
+    return float(np.max(np.abs(M.T @ M - np.eye(r1))))
+
+
+@pytest.mark.parametrize("dims,r_max", TWO_SIDED_CASES)
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_two_sided_parity(dims, r_max, dtype):
+    X = uniform_tensor(dims, seed=41)
+    if dtype == torch.float32:
+        X = X.astype(np.float32).astype(np.float64)
+    plan = api.TTSVDPlan(dims, r_max, 0.0, dtype, "df", two_sided=True)
+    plan.run(fortran_flat(X, dtype))
+    res = plan.result()
+    ref = tt_svd_two_sided(X, r_max)
+    assert res.ranks == ref.ranks, (res.ranks, ref.ranks)
+    tol = 1e-10 if dtype == torch.float64 else 1e-5
+    nx = np.linalg.norm(X)
+    cores = res.core_arrays()
+    err = np.linalg.norm(O.tt_full(cores) - X) / nx
+    err_ref = np.linalg.norm(O.tt_full(ref.cores) - X) / nx
+    assert abs(err - err_ref) <= tol, (err, err_ref)
+    assert abs(res.err2 - ref.err2) <= tol * nx * nx
+    # the order of the steps fixes which cores are left- and which right-orthonormal
+    d = len(dims)
+    a, b, t = 1, d, 0
+    while a < b:
+        if t % 2 == 0:
+            assert O.core_orthonormality_defect(cores[b - 1]) <= max(1e-12, tol), b
+            b -= 1
+        else:
+            assert _left_defect(cores[a - 1]) <= max(1e-12, tol), a
+            a += 1
+        t += 1
