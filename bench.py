@@ -202,7 +202,10 @@ def run_case(spec: str) -> int:
 
     G.build()
     capi.lib()
-    parts = spec.split(":")
+    parts = [x for x in spec.split(":") if "=" not in x]
+    for kv in (x for x in spec.split(":") if "=" in x):  # tuning keys, e.g. svd.block_nc=8
+        key, val = kv.split("=", 1)
+        capi.tt_tune_set(key, int(val))
     s = torch.cuda.current_stream()
     if parts[0] == "tsqr":
         rows, m = int(parts[1]), int(parts[2])

@@ -152,9 +152,13 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
   const int gid = tid / G, gl = tid % G, ngroups = nt / G;
   const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
 
+  __shared__ int s_cos;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) {
+      s_rot = 0;
+      s_cos = 0;
+    }
     __syncthreads();
     for (int rnd = 0; rnd < mp - 1; ++rnd) {
       for (int slot = gid; slot < mp / 2; slot += ngroups) {
@@ -200,12 +204,17 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
             vp[i] = fnmac(s, y, mul(c, x));
             vq[i] = fmac(s, x, mul(c, y));
           }
-          if (gl == 0) s_rot = 1;
+          if (gl == 0) {
+            s_rot = 1;
+            atomicMax(&s_cos, __float_as_int(gf / nf));  // |cos| >= 0: int order = float order
+          }
         }
       }
       __syncthreads();
     }
-    if (s_rot == 0) break;
+    // converged when nothing rotated, or when every rotation of the sweep had |cos| < 1e-7
+    // (the coupling left after it is of the order of those squared)
+    if (s_rot == 0 || __int_as_float(s_cos) < 1e-7f) break;
     __syncthreads();
   }
   if (sweep >= max_sweeps && tid == 0 && status) atomicOr(status, DEV_SVD_NOCONV);

@@ -318,6 +318,9 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
   cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
+// sweeps stop early once the largest |cos| rotated in a sweep is below this
+constexpr float kEarlyCos = 1e-7f;
+
 // ---- block-cyclic ordering ----------------------------------------------------------------
 // The MP = 2 NC npl columns (m padded with zero columns; npl even) form 2 NC blocks of npl
 // columns; CTA c holds a top and a bottom block.  A sweep is the circle method on blocks,
@@ -332,7 +335,8 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
 // rotate the pair (a_p, a_q) (and V's columns) by a group of G lanes; true if rotated
 template <class C, int G>
 __device__ __forceinline__ bool jacobi_pair(C* ap, C* aq, C* vp, C* vq, int m, int gl,
-                                            unsigned gmask, float tol, float floor_abs) {
+                                            unsigned gmask, float tol, float floor_abs,
+                                            float& maxcos) {
   auto al = lz(Tr<C>::zero()), be = al, ga = al;
   for (int r = gl; r < m; r += G) {
     const C x = ap[r], y = aq[r];
@@ -346,6 +350,7 @@ __device__ __forceinline__ bool jacobi_pair(C* ap, C* aq, C* vp, C* vq, int m, i
   const float gf = fabsf(hi32(gaf));
   const float nf = sqrtf(hi32(alf)) * sqrtf(hi32(bef));
   if (!(gf > tol * nf && nf > floor_abs && gf > 0.f)) return false;
+  maxcos = fmaxf(maxcos, gf / nf);
   const float zf = hi32(sub(bef, alf)) / (2.f * hi32(gaf));
   const float az = fabsf(zf);
   float tf = az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f)));
@@ -375,6 +380,7 @@ k_jacobi_block(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_
   __shared__ float s_red[32];
   __shared__ int s_any;
   __shared__ float s_fro;
+  __shared__ int s_cos, s_maxcos[2][16];
   const int m = m_ptr ? *m_ptr : m_max;
   const int NC = (int)cl.num_blocks();
   const int c = (int)cl.block_rank();
@@ -448,9 +454,13 @@ k_jacobi_block(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_
   int og = 0;  // outer rounds so far (buffer parity)
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) {
+      s_rot = 0;
+      s_cos = 0;
+    }
     __syncthreads();
     int rot = 0;
+    float mcos = 0.f;  // largest |cos| of a rotated pair in this sweep (this thread)
     for (int o = 0; o < 2 * NC - 1; ++o, ++og) {
       const int p = og & 1;
       C* TA = Ab + (2 * p) * bs;
@@ -474,7 +484,7 @@ k_jacobi_block(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_
             }
             rot |= jacobi_pair<C, G>(XA + (size_t)x * m_max, XA + (size_t)y * m_max,
                                      XV + (size_t)x * m_max, XV + (size_t)y * m_max, m, gl, gmask,
-                                     tol, floor_abs);
+                                     tol, floor_abs, mcos);
           }
           __syncthreads();
         }
@@ -485,7 +495,7 @@ k_jacobi_block(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_
           const int w2 = (u + k) % npl;
           rot |= jacobi_pair<C, G>(TA + (size_t)u * m_max, BA + (size_t)w2 * m_max,
                                    TV + (size_t)u * m_max, BV + (size_t)w2 * m_max, m, gl, gmask,
-                                   tol, floor_abs);
+                                   tol, floor_abs, mcos);
         }
         __syncthreads();
       }
@@ -493,8 +503,12 @@ k_jacobi_block(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_
       if (last) {
         // any rotation in this sweep: one flag per CTA into CTA 0 (read after the barrier)
         if (rot && gl == 0) s_rot = 1;
+        if (gl == 0 && mcos > 0.f) atomicMax(&s_cos, __float_as_int(mcos));  // |cos| >= 0
         __syncthreads();
-        if (tid == 0) flags0[(sweep & 1) * 16 + c] = s_rot;
+        if (tid == 0) {
+          flags0[(sweep & 1) * 16 + c] = s_rot;
+          cl.map_shared_rank(&s_maxcos[0][0], 0)[(sweep & 1) * 16 + c] = s_cos;
+        }
       }
       // move the blocks (circle method on blocks) into the other parity's buffers
       const int q = 1 - p;
@@ -524,9 +538,16 @@ k_jacobi_block(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_
       cl.sync();
     }
     if (tid == 0) {
-      int any = 0;
-      for (int k = 0; k < NC; ++k) any |= flags0[(sweep & 1) * 16 + k];
-      s_any = any;
+      int any = 0, mc = 0;
+      const int* mc0 = cl.map_shared_rank(&s_maxcos[0][0], 0);
+      for (int k = 0; k < NC; ++k) {
+        any |= flags0[(sweep & 1) * 16 + k];
+        mc = max(mc, mc0[(sweep & 1) * 16 + k]);
+      }
+      // converged when nothing rotated, or when every rotation of the sweep had
+      // |cos| < 1e-7: the coupling left after it is of the order of those squared
+      // (quadratic convergence), below the rotation threshold
+      s_any = any && __int_as_float(mc) >= kEarlyCos;
     }
     __syncthreads();
     if (s_any == 0) break;
@@ -720,32 +741,26 @@ cudaError_t launch_blk(const void* R, int64_t ldR, const int* m_dev, int m_max, 
 
 }  // namespace
 
-// Cluster size and block width for the block-cyclic kernel: minimises a per-sweep cost of
-// rounds x max(latency of a round, arithmetic of a round) + one block move per outer round
-// (all in microseconds, measured orders of magnitude on GB300); 0 if nothing fits.
+// Cluster size and block width for the block-cyclic kernel: 4 CTAs up to m = 96, else 16
+// (measured on GB300 for m = 64, 80, 128, 256 against 2, 4, 8 and 16), falling back to
+// the next size whose four block buffers fit in shared memory; 0 if none does.
 int jacobi_block_plan(Fmt comp, int m_max, int* npl_out) {
   const int forced = tune_get("svd.block_nc", 0);
-  double best = 1e30;
-  int best_nc = 0, best_npl = 0;
-  for (int nc : {2, 4, 8, 16}) {
-    if (forced && nc != forced) continue;
+  const int pref[4] = {m_max <= 96 ? 4 : 16, m_max <= 96 ? 8 : 8, m_max <= 96 ? 2 : 4, m_max <= 96 ? 16 : 2};
+  for (int c = 0; c < 4; ++c) {
+    const int nc = forced ? forced : pref[c];
     int npl = (m_max + 2 * nc - 1) / (2 * nc);
     npl += npl & 1;
     if (npl < 2) npl = 2;
-    if (npl * (m_max > 96 ? 32 : 16) > 1024) continue;
-    if (jacobi_block_smem(comp, m_max, nc, npl) > 220 * 1024) continue;
-    const double rounds = (npl - 1) + (2.0 * nc - 1) * npl;
-    const double work = npl * (double)m_max * 124.0 / 128.0 / 2000.0;  // us per round
-    const double lat = 0.3 + (double)m_max / (m_max > 96 ? 32.0 : 16.0) * 0.06;  // us per round
-    const double cost = rounds * std::max(lat, work) + (2 * nc - 1) * 1.5;
-    if (cost < best) {
-      best = cost;
-      best_nc = nc;
-      best_npl = npl;
+    const bool fits = npl * (m_max > 96 ? 32 : 16) <= 1024 &&
+                      jacobi_block_smem(comp, m_max, nc, npl) <= 220 * 1024;
+    if (fits) {
+      *npl_out = npl;
+      return nc;
     }
+    if (forced) return 0;
   }
-  if (best_nc) *npl_out = best_npl;
-  return best_nc;
+  return 0;
 }
 
 cudaError_t launch_jacobi_block(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
