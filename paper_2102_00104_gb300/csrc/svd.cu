@@ -433,8 +433,15 @@ template <class C, class RI>
 static void run_jacobi(const void* R, int64_t ldR, const int* m_dev, int m_max, void* Ag,
                        void* Vg, int ldA, int smem_ok, size_t smem, double* sigma, void* Vout,
                        int ldV, int* status, int* sweeps_out, int sweeps, cudaStream_t s) {
-  if (m_max <= 128)
+  // lanes per column pair: 16 up to m = 128 (measured on GB300 for m = 16..48 against 8
+  // and 32), tunable through "svd.g"
+  const int g = tune_get("svd.g", 16);
+  if (g == 32 && m_max <= 64)
+    run_jacobi_g<C, RI, 32>(R, ldR, m_dev, m_max, Ag, Vg, ldA, smem_ok, smem, sigma, Vout, ldV, status, sweeps_out, sweeps, s);
+  else if (g == 8 && m_max <= 128)
     run_jacobi_g<C, RI, 8>(R, ldR, m_dev, m_max, Ag, Vg, ldA, smem_ok, smem, sigma, Vout, ldV, status, sweeps_out, sweeps, s);
+  else if (m_max <= 128)
+    run_jacobi_g<C, RI, 16>(R, ldR, m_dev, m_max, Ag, Vg, ldA, smem_ok, smem, sigma, Vout, ldV, status, sweeps_out, sweeps, s);
   else if (m_max <= 256)
     run_jacobi_g<C, RI, 16>(R, ldR, m_dev, m_max, Ag, Vg, ldA, smem_ok, smem, sigma, Vout, ldV, status, sweeps_out, sweeps, s);
   else
