@@ -115,6 +115,20 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
   L.in = in;
   L.comp = comp;
   L.out = out;
+  if (!first && m_max >= tune_get("tsqr.merge_m", 96) && tsqr_merge_ok(m_max, in, comp) &&
+      rows % m_max == 0) {
+    // stacked triangles: binary tree of structured pairwise merges
+    const int64_t nblk = rows / m_max;
+    L.kind = 5;
+    L.maxm = m_max;
+    L.nw = 16;
+    L.pr = m_max;
+    L.panels = nblk;
+    L.ctas = (nblk + 1) / 2;
+    L.warps = L.ctas;
+    L.smem = 0;
+    return L;
+  }
   int64_t warps_cap;
   int cta_pr = 0, cta_nw = 0, cta_per_sm = 1;
   int cta_kind = 3;
@@ -141,8 +155,12 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
     int64_t ctas;
     if (first) {
       // the tree over the partial R's costs ~P m^3 against rows m^2 for this level:
-      // keep P <= rows / (4 m) so the tree stays a fraction of the work
-      const int64_t p_cap = std::max<int64_t>(1, rows / (4 * (int64_t)m_max));
+      // keep P <= rows / (4 m) so the tree stays a fraction of the work.  With the merge
+      // tree (m^3 / 6 per pair, log2 P deep) more and shorter first-level panels pay.
+      const bool merges = m_max >= tune_get("tsqr.merge_m", 96);
+      // rows per CTA >= q4 m / 4 (measured best: m rows for m >= 200, 2 m below)
+      const int64_t q4 = merges ? tune_get("tsqr.pcap_q", m_max >= 200 ? 4 : 8) : 16;
+      const int64_t p_cap = std::max<int64_t>(1, 4 * rows / (q4 * (int64_t)m_max));
       ctas = std::min<int64_t>(std::min<int64_t>(L.panels, (int64_t)nsm * cta_per_sm), p_cap);
       if (ctas_override > 0) ctas = std::min<int64_t>(L.panels, ctas_override);
     } else {
@@ -247,6 +265,7 @@ struct StepPlan {
   int m_max;
   int r_max_out;
   bool elide;
+  bool wide = false;  // rows < m: Jacobi on W^T directly, no TSQR (Sec. 3.1.2, R = [R_1; 0])
   Fmt in_fmt;
   int out_buf;   // -1: none (elided)
   std::vector<TsqrLevel> levels;
@@ -343,9 +362,13 @@ static tt_status build_plan(int d, const int64_t* n, int r_max, double tol, tt_d
     P.m_all_max = std::max(P.m_all_max, S.m_max);
     if (!S.elide) {
       const bool first_active = P.szR == 0;  // no TSQR planned yet
-      S.levels = plan_tsqr(rows, S.m_max, cur, P.comp_tsqr1, P.comp_tsqr2, nsm, ctas_override,
-                           first_active ? P.in_chunks : 1);
-      if (S.levels.empty()) return TT_ENOTIMPL;
+      S.wide = !first_active && rows < S.m_max && tune_get("svd.wide", 1) &&
+               jacobi_wide_fits(P.comp_svd, (int)rows, S.m_max);
+      if (!S.wide) {
+        S.levels = plan_tsqr(rows, S.m_max, cur, P.comp_tsqr1, P.comp_tsqr2, nsm, ctas_override,
+                             first_active ? P.in_chunks : 1);
+        if (S.levels.empty()) return TT_ENOTIMPL;
+      }
       for (auto& L : S.levels) {
         P.szR = std::max(P.szR, (size_t)L.warps * L.mb * S.m_max * fmt_bytes(L.out));
         P.szRscr = std::max(P.szRscr, tsqr_wide_scratch_bytes(L));
@@ -652,62 +675,69 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
       rows /= P.n[i - 2];
       continue;
     }
-    // TSQR levels
-    const void* lin = cur;
-    int64_t lld = rows;
-    void* Rfin = nullptr;
-    int64_t ldRfin = 0;
-    Fmt rfmt = Fmt::DF;
-    const double mm = (double)S.m_max;
-    for (size_t l = 0; l < S.levels.size(); ++l) {
-      const TsqrLevel& L = S.levels[l];
-      void* Rout = wb + P.off_R[l & 1];
-      const int64_t ldR = L.warps * L.mb;
-      if (L.chunks > 1) {
-        // first level in row blocks: block c (rows r0..r1 of every column) is copied from the
-        // host when X comes from there, and its launch waits only for that copy
-        prof::Scope ps(0, i, (double)L.rows * mm * fmt_bytes(L.in), 2.0 * (double)L.rows * mm * mm, s);
-        const size_t es = fmt_bytes(L.in);
-        for (int c = 0; c < L.chunks; ++c) {
-          const int64_t r0 = (int64_t)c * L.chunk_rows;
-          const int64_t r1 = std::min<int64_t>(L.rows, r0 + L.chunk_rows);
-          if (hin && hin->X_host && lin == X) {
-            TT_CK(cudaMemcpy2DAsync(static_cast<char*>(const_cast<void*>(X)) + r0 * es, lld * es,
-                                    hin->X_host + r0 * es, lld * es, (size_t)(r1 - r0) * es,
-                                    (size_t)S.m_max, cudaMemcpyHostToDevice, hin->cs));
-            TT_CK(cudaEventRecord(hin->ev[c], hin->cs));
-            TT_CK(cudaStreamWaitEvent(s, hin->ev[c], 0));
-          }
-          TsqrLevel Lc = L;
-          Lc.rows = r1 - r0;
-          Lc.panels = (Lc.rows + L.pr - 1) / L.pr;
-          Lc.chunks = 1;
-          Lc.warps = L.chunk_parts;
-          char* Rc = static_cast<char*>(Rout) + (size_t)c * L.chunk_parts * L.mb * fmt_bytes(L.out);
-          TT_CK(launch_tsqr_level(Lc, static_cast<const char*>(lin) + r0 * es, lld, &st->m[i], Rc,
-                                  ldR, wb + P.off_Rscr, status, s));
-          ++g_launches;
-        }
-      } else {
-        prof::Scope ps(l == 0 ? 0 : 1, i, (double)L.rows * mm * fmt_bytes(L.in),
-                       2.0 * (double)L.rows * mm * mm, s);
-        TT_CK(launch_tsqr_level(L, lin, lld, &st->m[i], Rout, ldR, wb + P.off_Rscr, status, s));
-        ++g_launches;
-      }
-      lin = Rout;
-      lld = ldR;
-      Rfin = Rout;
-      ldRfin = ldR;
-      rfmt = L.out;
-    }
-    // small SVD of R
     double* sig = reinterpret_cast<double*>(wb + P.off_sig);
     void* Vout = wb + P.off_Vout;
-    {
-      prof::Scope ps(2, i, 2.0 * mm * mm * fmt_bytes(P.comp_svd), 0.0, s, &st->sweeps[i]);
-      TT_CK(launch_jacobi(P.comp_svd, rfmt, Rfin, ldRfin, &st->m[i], S.m_max, wb + P.off_A,
-                          wb + P.off_V, P.ldA, sig, Vout, P.ldA, status, &st->sweeps[i], s));
+    const double mm = (double)S.m_max;
+    if (S.wide) {
+      prof::Scope ps(2, i, (double)rows * mm * fmt_bytes(cur_fmt), 0.0, s, &st->sweeps[i]);
+      TT_CK(launch_jacobi_wide(P.comp_svd, cur_fmt, cur, rows, (int)rows, &st->m[i], S.m_max, sig,
+                               Vout, P.ldA, status, &st->sweeps[i], s));
       ++g_launches;
+    } else {
+      // TSQR levels
+      const void* lin = cur;
+      int64_t lld = rows;
+      void* Rfin = nullptr;
+      int64_t ldRfin = 0;
+      Fmt rfmt = Fmt::DF;
+      for (size_t l = 0; l < S.levels.size(); ++l) {
+        const TsqrLevel& L = S.levels[l];
+        void* Rout = wb + P.off_R[l & 1];
+        const int64_t ldR = L.warps * L.mb;
+        if (L.chunks > 1) {
+          // first level in row blocks: block c (rows r0..r1 of every column) is copied from the
+          // host when X comes from there, and its launch waits only for that copy
+          prof::Scope ps(0, i, (double)L.rows * mm * fmt_bytes(L.in), 2.0 * (double)L.rows * mm * mm, s);
+          const size_t es = fmt_bytes(L.in);
+          for (int c = 0; c < L.chunks; ++c) {
+            const int64_t r0 = (int64_t)c * L.chunk_rows;
+            const int64_t r1 = std::min<int64_t>(L.rows, r0 + L.chunk_rows);
+            if (hin && hin->X_host && lin == X) {
+              TT_CK(cudaMemcpy2DAsync(static_cast<char*>(const_cast<void*>(X)) + r0 * es, lld * es,
+                                      hin->X_host + r0 * es, lld * es, (size_t)(r1 - r0) * es,
+                                      (size_t)S.m_max, cudaMemcpyHostToDevice, hin->cs));
+              TT_CK(cudaEventRecord(hin->ev[c], hin->cs));
+              TT_CK(cudaStreamWaitEvent(s, hin->ev[c], 0));
+            }
+            TsqrLevel Lc = L;
+            Lc.rows = r1 - r0;
+            Lc.panels = (Lc.rows + L.pr - 1) / L.pr;
+            Lc.chunks = 1;
+            Lc.warps = L.chunk_parts;
+            char* Rc = static_cast<char*>(Rout) + (size_t)c * L.chunk_parts * L.mb * fmt_bytes(L.out);
+            TT_CK(launch_tsqr_level(Lc, static_cast<const char*>(lin) + r0 * es, lld, &st->m[i], Rc,
+                                    ldR, wb + P.off_Rscr, status, s));
+            ++g_launches;
+          }
+        } else {
+          prof::Scope ps(l == 0 ? 0 : 1, i, (double)L.rows * mm * fmt_bytes(L.in),
+                         2.0 * (double)L.rows * mm * mm, s);
+          TT_CK(launch_tsqr_level(L, lin, lld, &st->m[i], Rout, ldR, wb + P.off_Rscr, status, s));
+          ++g_launches;
+        }
+        lin = Rout;
+        lld = ldR;
+        Rfin = Rout;
+        ldRfin = ldR;
+        rfmt = L.out;
+      }
+      // small SVD of R
+      {
+        prof::Scope ps(2, i, 2.0 * mm * mm * fmt_bytes(P.comp_svd), 0.0, s, &st->sweeps[i]);
+        TT_CK(launch_jacobi(P.comp_svd, rfmt, Rfin, ldRfin, &st->m[i], S.m_max, wb + P.off_A,
+                            wb + P.off_V, P.ldA, sig, Vout, P.ldA, status, &st->sweeps[i], s));
+        ++g_launches;
+      }
     }
     // rank choice, core
     {

@@ -47,7 +47,8 @@ struct TsqrLevel {
   int kind;          // 0 = narrow (warp, register panels), 1 = wide (warp, smem panels),
                      // 2 = CTA-cooperative (register panels, R in shared memory),
                      // 3 = column-owned CTA kernel (one barrier per column, look-ahead),
-                     // 4 = column-owned with the panel in shared memory (wide m)
+                     // 4 = column-owned with the panel in shared memory (wide m),
+                     // 5 = pairwise merge of the stacked triangles (upper levels only)
   int cfg;           // kind 2: layout id (see tsqr_cta.cu); kind 3: see tsqr_col.cu
   int maxm;          // narrow: 4/8/16 ; wide: 32*chunks (template bound)
   int mmax;          // worst-case m of this level (<= maxm)
@@ -85,6 +86,11 @@ size_t tsqr_cols_smem(int m_max, int prl);
 size_t tsqr_cols_scratch(int m_max, int64_t ctas);
 cudaError_t launch_tsqr_cols(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
                              void* Rout, int64_t ldR, void* Rscr, int* status, cudaStream_t s);
+// kind 5 (tsqr_merge.cu): one CTA merges two stacked R blocks with a structured Alg. 6 sweep
+bool tsqr_merge_ok(int m_max, Fmt in, Fmt comp);
+size_t tsqr_merge_scratch(int m_max, Fmt comp, int64_t ctas);
+cudaError_t launch_tsqr_merge(const TsqrLevel& L, const void* Rin, int64_t ldi, const int* m_dev,
+                              void* Rout, int64_t ldo, void* scr, int* status, cudaStream_t s);
 cudaError_t launch_tsqr_cta(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
                             void* Rout, int64_t ldR, void* Rscr, int* status, cudaStream_t s);
 
@@ -96,6 +102,12 @@ cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const i
                           int m_max, void* Ag, void* Vg, int ldA, double* sigma, void* Vout,
                           int ldV, int* status, int* sweeps_out, cudaStream_t s);
 size_t jacobi_scratch_bytes(Fmt comp, int m_max);
+// wide unfolding W (rows x m, rows < m, format win, leading dimension ldW): sigma and the
+// right singular vectors from one-sided Jacobi on W^T, no TSQR (one CTA, W^T in shared memory)
+bool jacobi_wide_fits(Fmt comp, int rows, int m_max);
+cudaError_t launch_jacobi_wide(Fmt comp, Fmt win, const void* W, int64_t ldW, int rows,
+                               const int* m_dev, int m_max, double* sigma, void* Vout, int ldV,
+                               int* status, int* sweeps_out, cudaStream_t s);
 // cluster form (svd_cluster.cu): cluster size for m (0 = single CTA) and its launch
 int jacobi_cluster_plan(Fmt comp, int m_max, int* npl_out);
 // block-cyclic cluster kernel: cluster size (0 if it does not apply) and columns per block

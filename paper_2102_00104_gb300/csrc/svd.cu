@@ -15,7 +15,7 @@
 // remaining small coupling).
 #include <mutex>
 
-#include "tsqr_kernels.cuh"
+#include "tsqr_col.cuh"
 #include "tt_svd.h"
 
 namespace tt {
@@ -242,6 +242,213 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
     sigma[rank] = sg;
     const C* vk = V + (size_t)k * ldA;
     for (int i = 0; i < m; ++i) Vout[i + (size_t)rank * ldV] = vk[i];
+  }
+}
+
+// ---- wide unfoldings (rows < columns) ---------------------------------------------
+// For W (rows x m) with rows < m the R of Alg. 2 has only `rows` nonzero rows, so its SVD
+// is that of W itself (a zero-padded R has the same nonzero sigma and V).  One-sided
+// Jacobi on the `rows` columns of A = W^T (each of length m) takes (rows/m)^2 of the
+// column pairs of the square form and accumulates nothing: at convergence the columns
+// are sigma_k v_k, so v_k = a_k / ||a_k||.  Columns at the rounding floor (the ones the
+// sweeps leave unrotated, see k_jacobi) and zero columns get an orthonormal completion
+// instead: unit vectors, Gram-Schmidt twice against the columns before them.
+template <class C, class WI, int G>
+__global__ void __launch_bounds__(1024)
+k_jacobi_wide(const WI* __restrict__ W, int64_t ldW, int rows, const int* __restrict__ m_ptr,
+              int m_max, int lda, double* __restrict__ sigma, C* __restrict__ Vout, int ldV,
+              int* status, int* sweeps_out, int max_sweeps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_rot;
+  __shared__ int s_cos;
+  __shared__ int s_exp;
+  __shared__ float s_red[32];
+  const int m = m_ptr ? *m_ptr : m_max;
+  const int nc = rows, ncp = rows + (rows & 1);
+  if (m < 1 || m > m_max || m > lda || nc < 1) {
+    if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
+    return;
+  }
+  C* A = reinterpret_cast<C*>(smem_raw);          // column p (= row p of W) at A + p * lda
+  C* nrm = A + (size_t)ncp * lda;                 // ||a_k||^2
+  int* defi = reinterpret_cast<int*>(nrm + ncp);  // by rank: 1 = completion needed
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nwarps = nt >> 5;
+
+  float mx = 0.f;
+  for (int idx = tid; idx < nc * m; idx += nt) {
+    const int p = idx % nc, i = idx / nc;
+    mx = fmaxf(mx, fabsf(fp32_hi(ld_as<C>(W[p + (int64_t)i * ldW]))));
+  }
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) s_red[wid] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < nwarps; ++w) t = fmaxf(t, s_red[w]);
+    int e = 0;
+    if (t > 0.f) frexpf(t, &e);
+    s_exp = e;
+  }
+  __syncthreads();
+  const int ex = s_exp;
+  for (int idx = tid; idx < ncp * m; idx += nt) {
+    const int p = idx % ncp, i = idx / ncp;
+    A[i + (size_t)p * lda] =
+        p < nc ? scale_pow2<C>(ld_as<C>(W[p + (int64_t)i * ldW]), -ex) : Tr<C>::zero();
+  }
+  __syncthreads();
+  float fro = 0.f;
+  for (int idx = tid; idx < ncp * m; idx += nt) {
+    const float v = fp32_hi(A[(idx % m) + (size_t)(idx / m) * lda]);
+    fro = fmaf(v, v, fro);
+  }
+  for (int o = 16; o; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+  if (lane == 0) s_red[wid] = fro;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < nwarps; ++w) t += s_red[w];
+    s_red[0] = t;
+  }
+  __syncthreads();
+  const float tol = conv_tol<C>(m);
+  const float floor_abs = tol * tol * s_red[0];
+  const int gid = tid / G, gl = tid % G, ngroups = nt / G;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) {
+      s_rot = 0;
+      s_cos = 0;
+    }
+    __syncthreads();
+    for (int rnd = 0; rnd < ncp - 1; ++rnd) {
+      for (int slot = gid; slot < ncp / 2; slot += ngroups) {
+        int p, q;
+        if (slot == 0) {
+          p = ncp - 1;
+          q = rnd;
+        } else {
+          p = (rnd + slot) % (ncp - 1);
+          q = (rnd - slot + ncp - 1) % (ncp - 1);
+        }
+        C* ap = A + (size_t)p * lda;
+        C* aq = A + (size_t)q * lda;
+        auto al = lz(Tr<C>::zero()), be = al, ga = al;
+        for (int i = gl; i < m; i += G) {
+          const C x = ap[i], y = aq[i];
+          al = lz_fmac(x, x, al);
+          be = lz_fmac(y, y, be);
+          ga = lz_fmac(x, y, ga);
+        }
+        const C alf = lz_fin(lz_gsum<G>(al, gmask));
+        const C bef = lz_fin(lz_gsum<G>(be, gmask));
+        const C gaf = lz_fin(lz_gsum<G>(ga, gmask));
+        const float gf = fabsf(fp32_hi(gaf));
+        const float nf = sqrtf(fp32_hi(alf)) * sqrtf(fp32_hi(bef));
+        if (gf > tol * nf && nf > floor_abs && gf > 0.f) {
+          const float zf = fp32_hi(sub(bef, alf)) / (2.f * fp32_hi(gaf));
+          const float az = fabsf(zf);
+          float tf = az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f)));
+          if (zf < 0.f) tf = -tf;
+          C c, s;
+          rot_cs(tf, c, s);
+          for (int i = gl; i < m; i += G) {
+            const C x = ap[i], y = aq[i];
+            ap[i] = fnmac(s, y, mul(c, x));
+            aq[i] = fmac(s, x, mul(c, y));
+          }
+          if (gl == 0) {
+            s_rot = 1;
+            atomicMax(&s_cos, __float_as_int(gf / nf));
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0 || __int_as_float(s_cos) < 1e-7f) break;
+    __syncthreads();
+  }
+  if (sweep >= max_sweeps && tid == 0 && status) atomicOr(status, DEV_SVD_NOCONV);
+  if (tid == 0 && sweeps_out) *sweeps_out = sweep + 1;
+
+  // sigma_k = ||a_k||, descending (stable by index); v_k = a_k / ||a_k||
+  for (int k = tid; k < nc; k += nt) {
+    auto acc = lz(Tr<C>::zero());
+    const C* ak = A + (size_t)k * lda;
+    for (int i = 0; i < m; ++i) acc = lz_fmac(ak[i], ak[i], acc);
+    nrm[k] = lz_fin(acc);
+  }
+  __syncthreads();
+  const int nout = nc < m ? nc : m;
+  for (int k = tid; k < nc; k += nt) {
+    const C nk = nrm[k];
+    int rank = 0;
+    for (int k2 = 0; k2 < nc; ++k2) {
+      if (k2 == k) continue;
+      const C n2 = nrm[k2];
+      if (is_gt(n2, nk) || (!is_gt(nk, n2) && k2 < k)) ++rank;
+    }
+    if (rank >= nout) continue;
+    const C sk = sqrt_(nk);
+    const double sg = ldexp(to_f64(sk), ex);
+    if (!isfinite(sg) && status) atomicOr(status, DEV_NONFINITE);
+    sigma[rank] = sg;
+    const bool low = !(fp32_hi(nk) > floor_abs);
+    defi[rank] = low ? 1 : 0;
+    if (!low) {
+      const C inv = rcp_(sk);
+      const C* ak = A + (size_t)k * lda;
+      for (int i = 0; i < m; ++i) Vout[i + (size_t)rank * ldV] = mul(ak[i], inv);
+    }
+  }
+  __syncthreads();
+  // completion of the columns at the rounding floor (they have the largest ranks)
+  if (wid != 0) return;
+  constexpr int QV = kMaxM / 32;
+  int cand = 0;
+  for (int p = 0; p < nout; ++p) {
+    if (!defi[p]) continue;
+    for (; cand < m; ++cand) {
+      C v[QV];
+#pragma unroll
+      for (int u = 0; u < QV; ++u)
+        v[u] = (lane + 32 * u == cand) ? Tr<C>::one() : Tr<C>::zero();
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int q = 0; q < p; ++q) {
+          const C* vq = Vout + (size_t)q * ldV;
+          auto acc = lz(Tr<C>::zero());
+#pragma unroll
+          for (int u = 0; u < QV; ++u) {
+            const int i = lane + 32 * u;
+            if (i < m) acc = lz_fmac(vq[i], v[u], acc);
+          }
+          const C h = colk::warp_allsum(lz_fin(acc));
+#pragma unroll
+          for (int u = 0; u < QV; ++u) {
+            const int i = lane + 32 * u;
+            if (i < m) v[u] = fnmac(h, vq[i], v[u]);
+          }
+        }
+      }
+      auto acc = lz(Tr<C>::zero());
+#pragma unroll
+      for (int u = 0; u < QV; ++u) acc = lz_fmac(v[u], v[u], acc);
+      const C n2 = colk::warp_allsum(lz_fin(acc));
+      if (fp32_hi(n2) > 0.25f) {
+        const C inv = rcp_(sqrt_(n2));
+#pragma unroll
+        for (int u = 0; u < QV; ++u) {
+          const int i = lane + 32 * u;
+          if (i < m) Vout[i + (size_t)p * ldV] = mul(v[u], inv);
+        }
+        __syncwarp();
+        ++cand;
+        break;
+      }
+    }
   }
 }
 
@@ -491,6 +698,62 @@ cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const i
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
+}
+
+bool jacobi_wide_fits(Fmt comp, int rows, int m_max) {
+  if (rows < 1 || rows >= m_max || m_max > kMaxM || (comp != Fmt::DF && comp != Fmt::F64))
+    return false;
+  const size_t es = fmt_bytes(comp);
+  const int ncp = rows + (rows & 1);
+  const size_t need = (size_t)ncp * m_max * es + (size_t)ncp * (es + sizeof(int));
+  return need <= max_smem_optin() - 4096;
+}
+
+template <class C, class WI, int G>
+static cudaError_t run_wide_g(const void* W, int64_t ldW, int rows, const int* m_dev, int m_max,
+                              double* sigma, void* Vout, int ldV, int* status, int* sweeps_out,
+                              cudaStream_t s) {
+  const int ncp = rows + (rows & 1);
+  const size_t es = sizeof(C);
+  const size_t smem = (size_t)ncp * m_max * es + (size_t)ncp * (es + sizeof(int));
+  int threads = ((ncp / 2) * G + 31) / 32 * 32;
+  if (threads < 64) threads = 64;
+  if (threads > 1024) threads = 1024;
+  auto k = k_jacobi_wide<C, WI, G>;
+  if (smem > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<1, threads, smem, s>>>(static_cast<const WI*>(W), ldW, rows, m_dev, m_max, m_max, sigma,
+                             static_cast<C*>(Vout), ldV, status, sweeps_out, 60);
+  return cudaGetLastError();
+}
+
+template <class C, class WI>
+static cudaError_t run_wide(const void* W, int64_t ldW, int rows, const int* m_dev, int m_max,
+                            double* sigma, void* Vout, int ldV, int* status, int* sweeps_out,
+                            cudaStream_t s) {
+  // lanes per column pair: about 8-16 elements of a column per lane
+  const int g = tune_get("svd.wide_g", m_max >= 256 ? 32 : m_max >= 64 ? 16 : 8);
+  if (g == 32) return run_wide_g<C, WI, 32>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+  if (g == 16) return run_wide_g<C, WI, 16>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+  return run_wide_g<C, WI, 8>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+}
+
+cudaError_t launch_jacobi_wide(Fmt comp, Fmt win, const void* W, int64_t ldW, int rows,
+                               const int* m_dev, int m_max, double* sigma, void* Vout, int ldV,
+                               int* status, int* sweeps_out, cudaStream_t s) {
+  if (!jacobi_wide_fits(comp, rows, m_max)) return cudaErrorInvalidValue;
+  if (comp == Fmt::DF && win == Fmt::DF)
+    return run_wide<df, df>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+  if (comp == Fmt::DF && win == Fmt::F64)
+    return run_wide<df, double>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+  if (comp == Fmt::DF && win == Fmt::F32)
+    return run_wide<df, float>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+  if (comp == Fmt::F64 && win == Fmt::F64)
+    return run_wide<double, double>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_truncate(const double* sigma, int64_t rows, int step_i, int n_next, int r_max,

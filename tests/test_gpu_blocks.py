@@ -81,6 +81,38 @@ def test_tsqr_rank_deficient_and_zero_columns():
     assert np.all(np.isfinite(Z)) and np.max(np.abs(Z)) < 1e-15
 
 
+def _row_signed(R):
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return R * d[:, None]
+
+
+# Above the first level, m >= 96 runs the tree of pairwise triangle merges: many
+# first-level R's (odd counts on the way up), m off a multiple of 32, FP32 panels
+# below FP64-class merges, and the widest m.
+@pytest.mark.parametrize("rows,m,dtype", [(30000, 96, torch.float64), (50000, 130, torch.float64),
+                                          (120000, 200, torch.float64), (60000, 400, torch.float64),
+                                          (20000, 257, torch.float64), (100000, 200, torch.float32),
+                                          (12000, 512, torch.float64), (8000, 130, torch.float64),
+                                          (6000, 200, torch.float64)])
+def test_tsqr_merge_tree(rows, m, dtype):
+    rng = np.random.default_rng(rows + 7 * m)
+    W = rng.standard_normal((rows, m))
+    if dtype == torch.float32:
+        W = W.astype(np.float32).astype(np.float64)
+    R = api.tsqr(colmajor(W, dtype)).cpu().numpy()
+    assert np.all(np.isfinite(R)) and np.allclose(np.tril(R, -1), 0)
+    nw2 = np.linalg.norm(W) ** 2
+    tol = 1e-12 if dtype == torch.float64 else 2e-5
+    assert np.max(np.abs(R.T @ R - W.T @ W)) <= tol * nw2
+    s_ref = sv(W)
+    assert np.max(np.abs(sv(R) - s_ref)) <= tol * s_ref[0]
+    if rows * m <= 1_200_000 and dtype == torch.float64:
+        # the oracle's flat Householder R, rows normalised to a positive diagonal
+        Ro = tsqr_flat(W, 64)
+        assert np.max(np.abs(_row_signed(R) - _row_signed(Ro))) <= 1e-10 * np.sqrt(nw2)
+
+
 @pytest.mark.parametrize("m,rank", [(64, 10), (80, 10), (128, 7), (32, 3), (200, 12), (400, 9)])
 def test_tsqr_low_rank_wide_panels(m, rank):
     # exactly low-rank W: after `rank` reflectors the panel columns hold only rounding

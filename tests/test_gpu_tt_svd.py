@@ -85,7 +85,8 @@ def test_d1_is_a_copy():
     assert np.array_equal(res.core_arrays()[0].ravel(), X)
 
 
-@pytest.mark.parametrize("dims,r_max", [((4,) * 8, 6), ((8, 8, 8, 8, 8), 10), ((3, 4, 5, 6, 7), 3)])
+@pytest.mark.parametrize("dims,r_max", [((4,) * 8, 6), ((8, 8, 8, 8, 8), 10), ((3, 4, 5, 6, 7), 3),
+                                        ((8,) * 7, 20)])
 def test_native_f64_arith_parity(dims, r_max):
     X = uniform_tensor(dims, seed=5)
     compare(X, run_gpu(X, r_max, arith="f64"), O.tt_svd(X, r_max), 1e-10)
@@ -98,7 +99,7 @@ def test_no_elide_matches(dims, r_max):
 
 
 @pytest.mark.parametrize("dims,rank,tol", [((4,) * 8, 3, 1e-4), ((5, 4, 6, 3, 4), 2, 1e-3),
-                                          ((3,) * 8, 4, 1e-2)])
+                                          ((3,) * 8, 4, 1e-2), ((4,) * 11, 3, 1e-4)])
 def test_tolerance_truncation(dims, rank, tol):
     X = planted_tt(dims, rank, seed=7, noise_rel=1e-6)
     ref = O.tt_svd(X, r_max=100, tol=tol)
@@ -109,13 +110,23 @@ def test_tolerance_truncation(dims, rank, tol):
     assert np.linalg.norm(O.tt_full(res.core_arrays()) - X) <= tol * np.linalg.norm(X)
 
 
+@pytest.mark.parametrize("dims,rank,r_max", [((4,) * 6, 1, 4), ((3, 4, 5, 6, 3), 2, 6),
+                                           ((8, 8, 8, 8), 3, 10)])
+def test_exact_low_rank_wide_steps(dims, rank, r_max):
+    # no noise: the wide unfoldings at the left end are rank-deficient, so some of the kept
+    # right singular vectors belong to zero singular values (the orthonormal completion)
+    X = planted_tt(dims, rank, seed=4, noise_rel=0.0)
+    compare(X, run_gpu(X, r_max), O.tt_svd(X, r_max), 1e-10)
+    compare(X, run_gpu(X, r_max, arith="f64"), O.tt_svd(X, r_max), 1e-10)
+
+
 def test_planted_rank_fp64():
     X = planted_tt((8, 8, 8, 8, 8), 4, seed=9, noise_rel=1e-6)
     compare(X, run_gpu(X, 10), O.tt_svd(X, 10), 1e-10)
 
 
 @pytest.mark.parametrize("dims,r_max", [((4,) * 10, 8), ((8, 8, 8, 8, 8), 10), ((2,) * 14, 32),
-                                        ((6, 5, 4, 3, 2), 50)])
+                                        ((6, 5, 4, 3, 2), 50), ((4,) * 10, 40)])
 def test_fp32_form_parity(dims, r_max):
     X64 = uniform_tensor(dims, seed=8)
     X32 = X64.astype(np.float32).astype(np.float64)
