@@ -60,8 +60,10 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--serve-seconds", type=float, default=4.0)
     p.add_argument("--case", default="", help="one building block for profiling instead of the bench: "
-                   "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix) or svd:M "
-                   "(small SVD of a uniform upper-triangular R); prints one JSON line")
+                   "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix), "
+                   "tsmm:ROWS:M:K (W V(:, 0:K) of a uniform FP64 W) or svd:M (small SVD of a "
+                   "uniform upper-triangular R), each optionally followed by :KEY=VALUE tuning "
+                   "keys; prints one JSON line")
     return p.parse_args()
 
 
@@ -173,22 +175,25 @@ def run_reference(args):
 
 
 # ---- the GPU arm ------------------------------------------------------------------------------
-def kernel_source_hash():
+def kernel_source_hash(files=None):
+    """Hash of the CUDA sources a kernel is built from (all of csrc/ when files is None)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2102_00104_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    names = sorted(files) if files else sorted(os.listdir(csrc))
+    for f in names:
         if f.endswith((".cu", ".cuh", ".h")):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def lookup_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from an ncu capture, if the kernel's sources are unchanged since."""
     try:
         t = json.load(open(TRAFFIC_JSON))
     except Exception:
         return None
     e = t.get(f"{kernel}|{workload}")
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(e.get("source_files")):
         return None
     return e.get("bytes_per_launch")
 
@@ -219,6 +224,15 @@ def run_case(spec: str) -> int:
         wp = (work.data_ptr() + 255) & ~255
         call = lambda: capi.tt_tsqr(W.data_ptr(), capi.TT_F64, rows, m, rows, R.data_ptr(), wp, wb,
                                     int(s.cuda_stream))
+    elif parts[0] == "tsmm":
+        rows, m, k = int(parts[1]), int(parts[2]), int(parts[3])
+        W = api.gen_uniform(rows * m, 3, torch.float64)
+        import numpy as np
+        Vh = np.linalg.qr(np.random.default_rng(0).standard_normal((m, m)))[0]
+        V = torch.from_numpy(np.asfortranarray(Vh).ravel(order="F").copy()).cuda()
+        Y = torch.empty(rows * k, dtype=torch.float64, device="cuda")
+        call = lambda: capi.tt_tsmm(W.data_ptr(), capi.TT_F64, rows, m, rows, V.data_ptr(), k,
+                                    Y.data_ptr(), rows, int(s.cuda_stream))
     elif parts[0] == "svd":
         m = int(parts[1])
         g = torch.Generator(device="cuda").manual_seed(0)

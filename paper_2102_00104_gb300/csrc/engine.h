@@ -156,18 +156,25 @@ cudaError_t launch_finish(const DevState* st, int d, int64_t* ranks_out, double*
 // Y (rows x r, ldy, format out) = W (rows x m, ld, format in) * V(:, 0:r)
 // (V format vfmt, ldV); m = m_dev[0], r = r_dev[0]; comp = arithmetic.
 struct TsmmCfg {
-  int kind;         // 0 = shared-memory tile of W, 1 = register-blocked (V in shared memory)
+  int kind;         // 0 = shared-memory tile of W, 1 = register-blocked (V in shared memory),
+                    // 2 = tensor cores, Ozaki splitting (float-float form)
   int cpt;          // kind 1: output columns per thread and pass
   Fmt in, comp, vfmt, out;
   int m_max, r_max;
   int tr;           // rows per tile
-  int rc;           // columns of V held in shared memory at a time
+  int rc;           // kind 0: columns of V held in shared memory at a time; kind 2: tile buffers
   int mstr;         // smem row stride (elements)
   size_t smem;
   int64_t ctas;
 };
 TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int64_t rows,
                   int num_sms);
+// the tensor-core form (tsmm_oz.cu): usable for these formats and sizes?
+bool tsmm_oz_ok(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max);
+size_t tsmm_oz_smem(int m_max, int r_max, int nbuf);
+cudaError_t launch_tsmm_oz(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
+                           const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
+                           int64_t ldy, int* status, cudaStream_t s);
 cudaError_t launch_tsmm(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
                         const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
                         int64_t ldy, int* status, cudaStream_t s);

@@ -225,6 +225,20 @@ TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int
   c.mstr = m_max | 1;
   const size_t es = fmt_bytes(comp);
   const size_t budget = 200 * 1024;
+  // float-float: the tensor-core form (Ozaki splitting) where its exact sums hold
+  if (tsmm_oz_ok(in, comp, vfmt, out, m_max, r_max)) {
+    c.kind = 2;
+    c.cpt = 0;
+    c.tr = 64;
+    // tile buffers per CTA: two (the next tile's copy overlaps this tile) or one
+    // (more CTAs per SM overlap each other's copies)
+    c.rc = tune_get("tsmm.oz_nbuf", 1) == 2 ? 2 : 1;
+    c.smem = tsmm_oz_smem(m_max, r_max, c.rc);
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (c.smem + 1024)));
+    const int64_t ntiles = (rows + 63) / 64;
+    c.ctas = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nsm * per_sm));
+    return c;
+  }
   // register-blocked form when V(:, 0:r) fits in shared memory
   // output columns per pass: the smallest instantiated width >= r_max (r_max = 50 runs as 2 x 25)
   static const int widths[] = {1, 2, 4, 5, 8, 10, 16, 20, 25, 32};
@@ -264,6 +278,7 @@ TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int
 cudaError_t launch_tsmm(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
                         const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
                         int64_t ldy, int* status, cudaStream_t s) {
+  if (c.kind == 2) return launch_tsmm_oz(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
 #define TT_TSMM(IN, CO, VF, OUT)                                                                \
   if (c.in == Fmt::IN && c.comp == Fmt::CO && c.vfmt == Fmt::VF && c.out == Fmt::OUT)           \
     return run<T_<Fmt::CO>, T_<Fmt::IN>, T_<Fmt::VF>, T_<Fmt::OUT>>(c, W, rows, ld, m_dev, V, ldV, \

@@ -150,7 +150,8 @@ def test_small_svd(m):
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 2e-6)])
 @pytest.mark.parametrize("rows,m,k", [(1, 1, 1), (1000, 8, 1), (5000, 8, 5), (33333, 40, 5),
-                                      (4096, 64, 20), (3000, 400, 50)])
+                                      (4096, 64, 20), (3000, 400, 50), (65536 + 192, 64, 10),
+                                      (20001, 80, 10), (12800, 96, 32), (70000, 17, 9)])
 def test_tsmm(dtype, tol, rows, m, k):
     rng = np.random.default_rng(rows + m + k)
     W = rng.standard_normal((rows, m))
