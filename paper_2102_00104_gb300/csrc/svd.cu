@@ -160,6 +160,8 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
       s_cos = 0;
     }
     __syncthreads();
+    bool rot_t = false;   // this thread's rotations and largest |cos|, combined per sweep
+    float mcos_t = 0.f;
     for (int rnd = 0; rnd < mp - 1; ++rnd) {
       for (int slot = gid; slot < mp / 2; slot += ngroups) {
         int p, q;
@@ -204,14 +206,19 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
             vp[i] = fnmac(s, y, mul(c, x));
             vq[i] = fmac(s, x, mul(c, y));
           }
-          if (gl == 0) {
-            s_rot = 1;
-            atomicMax(&s_cos, __float_as_int(gf / nf));  // |cos| >= 0: int order = float order
-          }
+          rot_t = true;
+          mcos_t = fmaxf(mcos_t, gf / nf);
         }
       }
       __syncthreads();
     }
+    const bool any_w = __any_sync(0xffffffffu, rot_t);
+    for (int o = 16; o; o >>= 1) mcos_t = fmaxf(mcos_t, __shfl_xor_sync(0xffffffffu, mcos_t, o));
+    if (lane == 0 && any_w) {
+      s_rot = 1;
+      atomicMax(&s_cos, __float_as_int(mcos_t));  // |cos| >= 0: int order = float order
+    }
+    __syncthreads();
     // converged when nothing rotated, or when every rotation of the sweep had |cos| < 1e-7
     // (the coupling left after it is of the order of those squared)
     if (s_rot == 0 || __int_as_float(s_cos) < 1e-7f) break;
@@ -324,6 +331,8 @@ k_jacobi_wide(const WI* __restrict__ W, int64_t ldW, int rows, const int* __rest
       s_cos = 0;
     }
     __syncthreads();
+    bool rot_t = false;   // this thread's rotations and largest |cos|, combined per sweep
+    float mcos_t = 0.f;
     for (int rnd = 0; rnd < ncp - 1; ++rnd) {
       for (int slot = gid; slot < ncp / 2; slot += ngroups) {
         int p, q;
@@ -360,14 +369,19 @@ k_jacobi_wide(const WI* __restrict__ W, int64_t ldW, int rows, const int* __rest
             ap[i] = fnmac(s, y, mul(c, x));
             aq[i] = fmac(s, x, mul(c, y));
           }
-          if (gl == 0) {
-            s_rot = 1;
-            atomicMax(&s_cos, __float_as_int(gf / nf));
-          }
+          rot_t = true;
+          mcos_t = fmaxf(mcos_t, gf / nf);
         }
       }
       __syncthreads();
     }
+    const bool any_w = __any_sync(0xffffffffu, rot_t);
+    for (int o = 16; o; o >>= 1) mcos_t = fmaxf(mcos_t, __shfl_xor_sync(0xffffffffu, mcos_t, o));
+    if (lane == 0 && any_w) {
+      s_rot = 1;
+      atomicMax(&s_cos, __float_as_int(mcos_t));
+    }
+    __syncthreads();
     if (s_rot == 0 || __int_as_float(s_cos) < 1e-7f) break;
     __syncthreads();
   }
