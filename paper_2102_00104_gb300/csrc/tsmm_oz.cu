@@ -345,7 +345,15 @@ k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
 }  // namespace
 
 bool tsmm_oz_ok(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max) {
-  if (tune_get("tsmm.oz", 1) == 0) return false;
+  // "tsmm.oz": 0 never, 1 where the float-float kernel is clearly ALU-bound, 2 whenever
+  // it applies.  Float-float costs ~12 FP32 instructions per m r product against
+  // 8 (m + r) bytes of traffic per row; with GB300's FP32 rate over its HBM bandwidth that
+  // is ALU-bound from m r / (m + r) ~ 3.4 on.  Measured on GB300: 2^27 x 8 -> 5 (ratio
+  // 3.1) 5.7 ms float-float vs 11.4 ms here; 2^24 x 40 -> 5 (4.4) 2.9 vs 3.1 ms;
+  // 2^24 x 64 -> 10 (8.6) 6.2 vs 4.7 ms; 2^21 x 80 -> 10 (8.9) 0.96 vs 0.87 ms.
+  const int mode = tune_get("tsmm.oz", 1);
+  if (mode == 0) return false;
+  if (mode == 1 && (m_max < 16 || m_max * r_max < 6 * (m_max + r_max))) return false;
   if (comp != Fmt::DF) return false;
   const bool types = (in == Fmt::F64 && vfmt == Fmt::DF && out == Fmt::DF) ||
                      (in == Fmt::DF && vfmt == Fmt::DF && out == Fmt::DF) ||
