@@ -116,9 +116,13 @@ def lib(path: str | None = None):
         f.restype = res
         f.argtypes = args
     _lib = L
-    # layouts chosen by the autotuner on this kind of GPU (tune_table.json), if present
+    # layouts chosen by the autotuner on this kind of GPU (tune_table.json), if present,
+    # then any overrides from the environment: TT_TUNE="key=value,key=value"
     from . import autotune
     autotune.load()
+    for kv in filter(None, os.environ.get("TT_TUNE", "").split(",")):
+        key, val = kv.split("=", 1)
+        check(L.tt_tune_set(key.strip().encode(), int(val)), "tt_tune_set (TT_TUNE)")
     return L
 
 

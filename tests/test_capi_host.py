@@ -152,3 +152,19 @@ def test_from_host_argument_checks(lib):
     misaligned = list(args)
     misaligned[10] = C.c_void_p(4097)
     assert lib.tt_svd_from_host(C.c_void_p(4096), C.c_void_p(4096), *misaligned) == capi.TT_EINVAL
+
+
+def test_tune_overrides_from_environment():
+    # TT_TUNE="key=value,..." is applied when the binding loads the library
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("from paper_2102_00104_gb300 import capi; capi.lib(); "
+            "print(capi.lib().tt_tune_set(b'tsmm.oz', 1))")
+    env = dict(os.environ, TT_TUNE="tsmm.oz=0, batched.streams=32")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    env["TT_TUNE"] = "tsmm.oz"  # no value: refused loudly
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True)
+    assert r.returncode != 0
