@@ -157,7 +157,8 @@ cudaError_t launch_finish(const DevState* st, int d, int64_t* ranks_out, double*
 // (V format vfmt, ldV); m = m_dev[0], r = r_dev[0]; comp = arithmetic.
 struct TsmmCfg {
   int kind;         // 0 = shared-memory tile of W, 1 = register-blocked (V in shared memory),
-                    // 2 = tensor cores, Ozaki splitting (float-float form)
+                    // 2 = tensor cores, Ozaki splitting (float-float form), mma.sync,
+                    // 3 = the same on tcgen05
   int cpt;          // kind 1: output columns per thread and pass
   Fmt in, comp, vfmt, out;
   int m_max, r_max;
@@ -173,6 +174,12 @@ TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int
 bool tsmm_oz_ok(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max);
 size_t tsmm_oz_smem(int m_max, int r_max, int nbuf);
 cudaError_t launch_tsmm_oz(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
+                           const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
+                           int64_t ldy, int* status, cudaStream_t s);
+// the same splitting on tcgen05 (tsmm_tc.cu)
+bool tsmm_tc_ok(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max);
+size_t tsmm_tc_smem(int m_max, int r_max);
+cudaError_t launch_tsmm_tc(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
                            const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
                            int64_t ldy, int* status, cudaStream_t s);
 cudaError_t launch_tsmm(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,

@@ -226,6 +226,16 @@ TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int
   const size_t es = fmt_bytes(comp);
   const size_t budget = 200 * 1024;
   // float-float: the tensor-core form (Ozaki splitting) where its exact sums hold
+  if (tsmm_tc_ok(in, comp, vfmt, out, m_max, r_max)) {
+    c.kind = 3;
+    c.cpt = 0;
+    c.tr = 128;
+    c.rc = 1;
+    c.smem = tsmm_tc_smem(m_max, r_max);
+    const int64_t ntiles = (rows + 127) / 128;
+    c.ctas = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nsm));
+    return c;
+  }
   if (tsmm_oz_ok(in, comp, vfmt, out, m_max, r_max)) {
     c.kind = 2;
     c.cpt = 0;
@@ -278,6 +288,7 @@ TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int
 cudaError_t launch_tsmm(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
                         const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
                         int64_t ldy, int* status, cudaStream_t s) {
+  if (c.kind == 3) return launch_tsmm_tc(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
   if (c.kind == 2) return launch_tsmm_oz(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
 #define TT_TSMM(IN, CO, VF, OUT)                                                                \
   if (c.in == Fmt::IN && c.comp == Fmt::CO && c.vfmt == Fmt::VF && c.out == Fmt::OUT)           \

@@ -26,11 +26,13 @@
 
 #include <algorithm>
 
-#include "tsqr_kernels.cuh"
+#include "ozaki.cuh"
 
 namespace tt {
 
 namespace {
+
+using namespace ozk;
 
 constexpr int OZ_TR = 64;               // rows per tile
 constexpr int OZ_WARPS = 4;
@@ -38,100 +40,6 @@ constexpr int OZ_THREADS = 32 * OZ_WARPS;
 constexpr int OZ_CS = OZ_TR * 8 + 32;   // bytes per staged column (padded: conflict-free reads)
 constexpr int OZ_MAXM = 96;             // sum of one level over k stays below 2^24
 constexpr int OZ_MAXR = 32;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void oz_bar_init(uint64_t* b) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ void oz_expect(uint64_t* b, uint32_t bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
-                   smem_u32(b)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void oz_bulk(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(b))
-      : "memory");
-}
-__device__ __forceinline__ bool oz_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// wait for the phase with this parity; false after about kWaitCycles
-__device__ __forceinline__ bool oz_wait(uint64_t* b, uint32_t parity) {
-  if (oz_try(b, parity)) return true;
-  const long long t0 = clock64();
-  while (!oz_try(b, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
-  return true;
-}
-
-// biased exponent of |x| as if x were FP32 (x < 2^(be - 126)); 0 for zero
-__device__ __forceinline__ int oz_bexp(df x) { return (__float_as_int(x.hi) >> 23) & 0xFF; }
-__device__ __forceinline__ int oz_bexp(double x) {
-  const int e = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
-  // FP64 exponent e - 1023 = FP32 biased exponent - 127; clamp into FP32's range
-  const int f = e - 896;
-  return e == 0 ? 0 : (f < 1 ? 1 : (f > 254 ? 254 : f));
-}
-// a word whose maximum over a row gives the row's largest exponent (oz_bexp_of)
-__device__ __forceinline__ unsigned oz_key(df x) { return (unsigned)__float_as_int(x.hi) & 0x7F800000u; }
-__device__ __forceinline__ unsigned oz_key(double x) {
-  return (unsigned)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7FF00000u;
-}
-__device__ __forceinline__ int oz_bexp_of(unsigned key, df*) { return (int)(key >> 23); }
-__device__ __forceinline__ int oz_bexp_of(unsigned key, double*) {
-  const int e = (int)(key >> 20);
-  const int f = e - 896;
-  return e == 0 ? 0 : (f < 1 ? 1 : (f > 254 ? 254 : f));
-}
-// 2^-E with E = be - 126, for scaling values into (-1, 1)
-__device__ __forceinline__ float oz_inv_scale(int be) {
-  const int s = 253 - be;  // biased exponent of 2^(126 - be)
-  return __int_as_float((s < 1 ? 1 : (s > 254 ? 254 : s)) << 23);
-}
-// 2^e as FP32 (0 below the normal range)
-__device__ __forceinline__ float oz_pow2(int e) {
-  const int b = e + 127;
-  return b < 1 ? 0.f : __int_as_float((b > 254 ? 254 : b) << 23);
-}
-
-// six digits of (hi + lo) 2^-E (see the header); d[a-1] = d_a.  Rounding to the nearest
-// integer by adding and subtracting 1.5 * 2^23 (|t| <= 256 here): FMA-pipe operations only.
-__device__ __forceinline__ void oz_digits(df x, float sc, float (&d)[6]) {
-  constexpr float M = 12582912.f;  // 1.5 * 2^23
-  float rem = x.hi * sc;
-  const float sl = x.lo * sc;
-  d[0] = __fsub_rn(__fmaf_rn(rem, 128.f, M), M);
-  rem = __fmaf_rn(rem, 128.f, -d[0]);
-  d[1] = __fsub_rn(__fmaf_rn(rem, 256.f, M), M);
-  rem = __fmaf_rn(rem, 256.f, -d[1]);
-  d[2] = __fsub_rn(__fmaf_rn(rem, 256.f, M), M);
-  rem = __fmaf_rn(rem, 256.f, -d[2]);
-  const float t = __fmaf_rn(sl, 2147483648.f, rem * 256.f);  // the low word enters at weight 2^31
-  d[3] = __fsub_rn(__fadd_rn(t, M), M);
-  rem = __fsub_rn(t, d[3]);
-  d[4] = __fsub_rn(__fmaf_rn(rem, 256.f, M), M);
-  rem = __fmaf_rn(rem, 256.f, -d[4]);
-  d[5] = __fsub_rn(__fmaf_rn(rem, 256.f, M), M);
-}
-
-// two digits as a bf16 pair: a digit has at most 8 significant bits, so its bf16 is the
-// upper half of its FP32 word; the smaller k goes to the low half
-__device__ __forceinline__ uint32_t oz_pack(float lo_k, float hi_k) {
-  return __byte_perm(__float_as_uint(lo_k), __float_as_uint(hi_k), 0x7632);
-}
 
 __device__ __forceinline__ void oz_mma(float (&c)[4], const uint32_t (&a)[4], uint2 b) {
   asm volatile(
@@ -141,8 +49,6 @@ __device__ __forceinline__ void oz_mma(float (&c)[4], const uint32_t (&a)[4], ui
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
 }
 
-template <class S>
-__device__ __forceinline__ S oz_zero() { return S{}; }
 
 // NT n-tiles of 8 output columns (r <= 8 NT).  Shared memory: two tile buffers
 // (m_max columns of OZ_CS bytes each), V's digits in B-fragment order

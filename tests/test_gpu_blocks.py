@@ -183,3 +183,19 @@ def test_small_svd_rank_deficient(m, rank):
     scale = max(s_ref[0], 1.0)
     assert np.max(np.abs(sig - s_ref)) <= 1e-12 * scale
     assert np.max(np.abs(V.T @ V - np.eye(m))) <= 1e-13 * max(m, 10)
+
+
+@pytest.mark.parametrize("rows,m,k", [(65536 + 128, 64, 10), (20001, 80, 10), (12800, 64, 20),
+                                      (70000, 33, 9)])
+def test_tsmm_tcgen05(rows, m, k):
+    # the tcgen05 form of the tensor-core W V_r (opt-in tuning key "tsmm.tc")
+    rng = np.random.default_rng(rows + 7 * m + k)
+    W = rng.standard_normal((rows, m))
+    V = np.linalg.qr(rng.standard_normal((m, m)))[0]
+    capi.tt_tune_set("tsmm.tc", 1)
+    try:
+        Y = api.tsmm(colmajor(W, torch.float64), torch.from_numpy(V).cuda(), k).cpu().numpy().T
+    finally:
+        capi.tt_tune_set("tsmm.tc", 0)
+    ref = W @ V[:, :k]
+    assert np.max(np.abs(Y - ref)) <= 1e-13 * np.max(np.abs(W)) * np.sqrt(m)
