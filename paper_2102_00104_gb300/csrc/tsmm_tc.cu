@@ -12,12 +12,15 @@
 // K-major layout of the MMA (core matrices of 8 rows x 16 bytes: the core of row group g
 // and k-group kg at g * 256 kt + kg * 128 bytes; the next core along K at +128 bytes, the
 // next along M at +256 kt).  V's digits sit in six planes of the same layout (N = 16 or 32
-// rows).  Thread 0 then issues, per k-step of 16, the 21 digit products a + b <= 5
-// (tcgen05.mma.kind::f16, bf16 in, FP32 accumulate, N = 16 or 32) into the accumulator of
-// level a + b, commits them to an mbarrier, and starts the bulk copy of the next tile
-// into the freed tile buffer.  The accumulators are read back with tcgen05.ld (warp w
-// reads lanes 32 (w mod 4) .. of tensor memory, column group w / 4) and added in
-// float-float from the smallest level, as in tsmm_oz.cu.
+// rows, contiguous, so that planes b = 0..5-a form one operand of N = 16 (6 - a) rows).
+// Thread 0 then issues, per k-step of 16, one tcgen05.mma.kind::f16 per digit a of W
+// (bf16 in, FP32 accumulate, M = 128, N = 16 (6 - a)) against V's digits 0..5-a, into
+// its own block of tensor-memory columns (336 of 512: the block of (a, b) holds the
+// product of digits a and b), commits them to an mbarrier, and starts the bulk copy of
+// the next tile into the freed tile buffer.  The products are read back with tcgen05.ld
+// (warp w reads lanes 32 (w mod 4) .. of tensor memory, output columns 4 (w / 4) ..),
+// the ones of a level a + b are summed (exactly: the level's sum stays below 2^24), and
+// the levels are added in float-float from the smallest, as in tsmm_oz.cu.
 //
 // Every wait is bounded (kWaitCycles); a CTA whose wait runs out sets DEV_ERR_TIMEOUT,
 // lets the copies it issued land (bounded), frees its tensor memory and returns.
@@ -71,17 +74,6 @@ __device__ __forceinline__ void tc_ld<4>(uint32_t taddr, float (&v)[4]) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
-template <>
-__device__ __forceinline__ void tc_ld<8>(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                 "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -89,9 +81,9 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// NN = N of one MMA (16 or 32 output columns, r <= NN).  Shared memory: the W tile (m_max
-// columns of TC_CS bytes), six A digit planes (128 x 16 kt bf16 each), six B digit planes
-// (NN x 16 kt bf16 each), the row and column exponents, two mbarriers, the TMEM address.
+// NN = 16 output columns (r <= 16).  Shared memory: the W tile (m_max columns of TC_CS
+// bytes), six A digit planes (128 x 16 kt bf16 each), six B digit planes (NN x 16 kt bf16
+// each, contiguous), the row and column exponents, two mbarriers, the TMEM address.
 template <int NN, class S, class VS, class SO>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tsmm_tc(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
@@ -99,7 +91,8 @@ k_tsmm_tc(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
           SO* __restrict__ Y, int64_t ldy, int m_max, int r_max, int* status) {
   constexpr int NL = 6;                // levels 2..7
   constexpr int CPW = NN / 4;          // output columns per warp in the read-back
-  constexpr uint32_t TMCOLS = NL * NN <= 128 ? 128 : 256;
+  constexpr uint32_t TMCOLS = 512;     // 21 blocks of NN columns (336)
+  static_assert(NN == 16, "one MMA per digit of W needs 21 NN-column blocks within 512");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int m = m_ptr ? *m_ptr : m_val;
   const int r = r_ptr ? *r_ptr : r_val;
@@ -172,7 +165,8 @@ k_tsmm_tc(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  constexpr uint32_t idesc = tc_idesc(NN);
+  // first tensor-memory column of the products of W's digit a (blocks b = 0..5-a)
+  auto colbase = [](int a) { return NN * (6 * a - a * (a - 1) / 2); };
 
   int nissued = 0, nwaited = 0;  // tile copies (thread 0's count, for a clean exit)
   auto issue = [&](int64_t tile) {
@@ -243,16 +237,12 @@ k_tsmm_tc(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
     tc_fence_after();
     if (tid == 0) {
       const uint32_t a0 = smem_u32(Ap), b0 = smem_u32(Bp);
-      unsigned wrote = 0;
       for (int kk = 0; kk < kt; ++kk)
-        for (int a = 0; a < 6; ++a)
-          for (int b = 0; a + b <= 5; ++b) {
-            const int L = a + b;
-            const uint64_t ad = tc_desc(a0 + (uint32_t)(a * aplane) + 256u * kk, sbo);
-            const uint64_t bd = tc_desc(b0 + (uint32_t)(b * bplane) + 256u * kk, sbo);
-            tc_mma(tmem + (uint32_t)(L * NN), ad, bd, idesc, (wrote >> L) & 1u);
-            wrote |= 1u << L;
-          }
+        for (int a = 0; a < 6; ++a) {
+          const uint64_t ad = tc_desc(a0 + (uint32_t)(a * aplane) + 256u * kk, sbo);
+          const uint64_t bd = tc_desc(b0 + 256u * kk, sbo);  // V's digit planes 0 .. 5 - a
+          tc_mma(tmem + (uint32_t)colbase(a), ad, bd, tc_idesc(NN * (6 - a)), kk > 0 ? 1u : 0u);
+        }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               smem_u32(&bar[1]))
@@ -268,8 +258,21 @@ k_tsmm_tc(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
       float acc[NL][CPW];
 #pragma unroll
       for (int L = 0; L < NL; ++L)
-        tc_ld<CPW>(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(L * NN + cg * CPW), acc[L]);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int cn = 0; cn < CPW; ++cn) acc[L][cn] = 0.f;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        // the products of digit a with V's digits 0 .. 5-a: all loads, then one wait
+        float v[6][CPW];
+#pragma unroll
+        for (int b = 0; a + b <= 5; ++b)
+          tc_ld<CPW>(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(colbase(a) + b * NN + cg * CPW), v[b]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int b = 0; a + b <= 5; ++b)
+#pragma unroll
+          for (int cn = 0; cn < CPW; ++cn) acc[a + b][cn] += v[b][cn];  // exact: integers < 2^24
+      }
       const int rr = 32 * wq + lane;
       const int64_t row = r0 + rr;
       const int E = Erow[rr] - 126;
@@ -332,8 +335,7 @@ template <class S, class VS, class SO>
 cudaError_t run_tc_nn(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, const int* m_dev,
                       const void* V, int ldV, const int* r_dev, void* Y, int64_t ldy, int* status,
                       cudaStream_t s) {
-  if (c.r_max <= 16) return run_tc<16, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-  return run_tc<32, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+  return run_tc<16, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
 }
 
 }  // namespace
@@ -342,12 +344,17 @@ cudaError_t run_tc_nn(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
 bool tsmm_tc_ok(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max) {
   if (tune_get("tsmm.tc", 0) == 0) return false;
   if (!tsmm_oz_ok(in, comp, vfmt, out, m_max, r_max)) return false;
-  if (m_max > TC_MAXM || r_max > 32) return false;
+  if (m_max > TC_MAXM || r_max > 16) return false;
   // dynamic shared memory plus the 2 KB of the static row-key array
-  return tc_smem(m_max, r_max <= 16 ? 16 : 32) + 4 * TC_TR * sizeof(unsigned) <= 227 * 1024;
+  return tc_smem(m_max, 16) + 4 * TC_TR * sizeof(unsigned) <= 227 * 1024;
 }
 
-size_t tsmm_tc_smem(int m_max, int r_max) { return tc_smem(m_max, r_max <= 16 ? 16 : 32); }
+// at least half of an SM's shared memory: one CTA per SM, so the 512 tensor-memory
+// columns a CTA allocates are always free when it starts
+size_t tsmm_tc_smem(int m_max, int r_max) {
+  (void)r_max;
+  return std::max<size_t>(tc_smem(m_max, 16), 120 * 1024);
+}
 
 cudaError_t launch_tsmm_tc(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
                            const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
