@@ -1,0 +1,56 @@
+"""Parity at the full size of the benchmark: an 8^10 FP64 tensor (2^30 entries, 8 GiB),
+uniform[0,1) from the same seed and with the same plan as bench.py, r_max = 10.
+
+The oracle cannot decompose 8 GiB in a test, so the run is checked against what holds
+at any size:
+* ranks: the tol = 0 rule of Alg. 1 (r_{i-1} = min(r_max, rows, cols)), bit-exact;
+* the first computed step (i = 9; step 10 is elided, which is exact) returns the singular
+  values of the unfolding X_(8) (2^24 x 64): compared with the square roots of the
+  eigenvalues of its FP64 Gram matrix, formed on the host (LAPACK; accurate to ~1e-15
+  relative here, the unfolding being well conditioned);
+* the sum of that step's sigma^2 equals ||X||_F^2;
+* cores 2..10 have orthonormal rows;
+* ||X - X~||_F^2 equals the reported discarded energy (successive orthogonal projections),
+  with X~ contracted on the host.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import tt_svd_oracle as O
+from paper_2102_00104_gb300 import api
+from tests.gpu_common import ensure_lib
+
+pytestmark = pytest.mark.gpu
+
+
+def test_full_size_8p10_rmax10():
+    ensure_lib()
+    dims, r_max = (8,) * 10, 10
+    nbar = 8 ** 10
+    X = api.gen_uniform(nbar, 0, torch.float64)  # the bench's input (seed 0)
+    plan = api.TTSVDPlan(dims, r_max, 0.0, torch.float64, "df", want_sigma=True)
+    plan.run(X)
+    res = plan.result()
+    assert res.ranks == O.planned_ranks(list(dims), r_max)
+
+    Xh = X.cpu().numpy()
+    del X
+    W8 = Xh.reshape(64, 8 ** 8)  # row c = column c of the unfolding X_(8) (Fortran order)
+    G = W8 @ W8.T
+    ev = np.linalg.eigvalsh(G)[::-1]
+    s_ref = np.sqrt(np.maximum(ev, 0.0))
+    assert s_ref[-1] > 1e-3 * s_ref[0]  # well conditioned: the Gram route is accurate
+    got = res.sigma[9].cpu().numpy()
+    assert got.shape[0] >= 64
+    assert np.max(np.abs(got[:64] - s_ref)) <= 1e-10 * s_ref[0], np.max(np.abs(got[:64] - s_ref))
+    nx2 = float(np.trace(G))
+    assert abs(float(np.sum(got[:64] ** 2)) - nx2) <= 1e-12 * nx2
+
+    cores = res.core_arrays()
+    for c in cores[1:]:
+        assert O.core_orthonormality_defect(c) <= 1e-12
+    Xt = O.tt_full(cores).ravel(order="F")
+    d = Xh - Xt
+    err2 = float(np.dot(d, d))
+    assert abs(err2 - res.err2) <= 1e-10 * nx2, (err2, res.err2, nx2)
