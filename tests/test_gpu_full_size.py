@@ -55,3 +55,29 @@ def test_full_size_8p10_rmax10():
     d = Xh - Xt
     err2 = float(np.dot(d, d))
     assert abs(err2 - res.err2) <= 1e-10 * nx2, (err2, res.err2, nx2)
+
+
+def test_full_size_8p10_fp32_form_rmax32():
+    # the precision form at full size: the same 2^30 entries stored FP32 (4 GiB), r_max = 32;
+    # reference values from the FP32 values widened to FP64, bar 1e-5 (relative to sigma_max)
+    ensure_lib()
+    dims, r_max = (8,) * 10, 32
+    X = api.gen_uniform(8 ** 10, 0, torch.float32)
+    plan = api.TTSVDPlan(dims, r_max, 0.0, torch.float32, "df", want_sigma=True)
+    plan.run(X)
+    res = plan.result()
+    assert res.ranks == O.planned_ranks(list(dims), r_max)
+    Xh = X.cpu().numpy().astype(np.float64)
+    del X
+    W8 = Xh.reshape(64, 8 ** 8)
+    G = W8 @ W8.T
+    s_ref = np.sqrt(np.maximum(np.linalg.eigvalsh(G)[::-1], 0.0))
+    got = res.sigma[9].cpu().numpy()
+    assert np.max(np.abs(got[:64] - s_ref)) <= 1e-5 * s_ref[0]
+    cores = res.core_arrays()
+    for c in cores[1:]:
+        assert O.core_orthonormality_defect(c) <= 1e-5
+    Xt = O.tt_full(cores).ravel(order="F")
+    d = Xh - Xt
+    nx2 = float(np.trace(G))
+    assert abs(float(np.dot(d, d)) - res.err2) <= 1e-5 * nx2
