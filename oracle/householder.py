@@ -5,7 +5,7 @@ Test infrastructure only (see ``oracle/__init__.py``).
 Alg. 6 transforms a rectangle M (n_b x m) stacked on an upper triangle R (m x m)
 into a new triangle R_bar with [M; R] = Q R_bar, without forming or storing Q
 and without modifying M.  The index windows printed in the paper are garbled;
-the reading used here (listed in the design doc) is the mathematical content: the
+the reading used here is the mathematical content: the
 reflector of column j acts on all n_b rows of M and on row j of R, with the
 pivot element R[j, j]; rows 0..j-1 of R are final and untouched, rows j+1..m-1
 of R are zero in column j and therefore unaffected.

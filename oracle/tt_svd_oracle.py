@@ -7,7 +7,7 @@ are Fortran ordered (n_1 fastest), every reshape is a Fortran-order reshape,
 and cores are T^(i) in R^{r_{i-1} x n_i x r_i} with r_0 = r_d = 1 (Sec. 2.1.2).
 Step ``i`` runs from d down to 2 (right to left), as in Alg. 1.
 
-Readings of the paper used here (each one is listed in the design doc):
+Readings of the paper used here (where it is silent or ambiguous):
 * tol == 0 means "no tolerance truncation": r_delta = number of singular values.
 * The tail test of Alg. 1 line 8 uses "<=" as printed; the tail runs over all
   min(rows, cols) singular values of the unfolding.

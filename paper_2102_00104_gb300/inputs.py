@@ -89,7 +89,7 @@ def uniform_tensor(dims, seed: int, chunk: int = 1 << 24) -> np.ndarray:
 
 
 def planted_tt(dims, rank: int, seed: int, noise_rel: float = 1e-6) -> np.ndarray:
-    """A tensor with planted TT ranks plus relative Gaussian noise (recipe in the design doc).
+    """A tensor with planted TT ranks plus relative Gaussian noise (relative noise level).
 
     Cores are i.i.d. N(0,1) with ranks r_k = min(rank, n_1..n_k, n_{k+1}..n_d);
     the contraction is done in FP64, scaled to ||X||_F = 1, and noise E with
