@@ -1,20 +1,30 @@
 // tsqr.cu -- instantiation and launch of the TSQR level kernels.
-#include "tsqr_kernels.cuh"
+#include "tsqr_narrow.cuh"
 
 namespace tt {
 
 namespace {
 
-template <int MAXM, class C, class S, class RO>
-cudaError_t run_narrow(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout,
-                       int64_t ldR, int* status, cudaStream_t s) {
-  constexpr int K = 64 / MAXM;
+template <int MAXM, int K, class C, class S, class RO>
+cudaError_t run_narrow_k(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout,
+                         int64_t ldR, int* status, cudaStream_t s) {
   constexpr int NW = 4;
   if (L.nw < 1 || L.nw > NW) return cudaErrorInvalidValue;
   k_tsqr_narrow<MAXM, K, NW, C, S, RO><<<(unsigned)L.ctas, L.nw * 32, 0, s>>>(
       static_cast<const S*>(W), L.rows, ld, m_dev, L.mval, static_cast<RO*>(Rout), ldR, L.mb,
-      L.panels, status);
+      L.panels, status, tune_get("tsqr.narrow_norm", 1));
   return cudaGetLastError();
+}
+
+// rows per lane K = panel rows / 32: 64 / MAXM or 32 / MAXM (fewer registers, more warps)
+template <int MAXM, class C, class S, class RO>
+cudaError_t run_narrow(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout,
+                       int64_t ldR, int* status, cudaStream_t s) {
+  if (L.pr == 32 * (64 / MAXM))
+    return run_narrow_k<MAXM, 64 / MAXM, C, S, RO>(L, W, ld, m_dev, Rout, ldR, status, s);
+  if (L.pr == 32 * (32 / MAXM))
+    return run_narrow_k<MAXM, 32 / MAXM, C, S, RO>(L, W, ld, m_dev, Rout, ldR, status, s);
+  return cudaErrorInvalidValue;
 }
 
 template <int NCH, class C, class S, class RO>

@@ -14,8 +14,7 @@
 // The warp finally writes R as one block of the stacked output, so the next
 // level is the same kernel applied to the tall matrix of stacked R's.
 //
-// narrow kernel (m <= MAXM <= 16): lane l holds rows l, l+32, ... of the panel
-//   in registers; dot products are reduced with warp butterflies.
+// narrow kernel (m <= MAXM <= 16): tsqr_narrow.cuh.
 // wide kernel (m <= 32*NCH): the panel sits in shared memory (row-major, odd
 //   row stride), lane l owns columns l, l+32, ...; each lane computes whole
 //   dot products, so a column step needs only two broadcasts; R lives in a
@@ -30,99 +29,6 @@ template <Fmt F> struct FT;
 template <> struct FT<Fmt::F64> { using T = double; };
 template <> struct FT<Fmt::DF> { using T = df; };
 template <> struct FT<Fmt::F32> { using T = float; };
-
-template <int MAXM, int K, int NW, class C, class S, class RO>
-__global__ void __launch_bounds__(NW * 32)
-k_tsqr_narrow(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
-              int m_val, RO* __restrict__ Rout, int64_t ldR, int mb, int64_t npanels, int* status) {
-  constexpr int PR = 32 * K;
-  __shared__ C Rsh[NW][MAXM][MAXM];
-  const int m = m_ptr ? *m_ptr : m_val;
-  const int nwb = blockDim.x >> 5;
-  if (m < 1 || m > MAXM || m > mb || nwb > NW) {
-    if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
-    return;
-  }
-  const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * nwb + w;
-  const int64_t nwt = (int64_t)gridDim.x * nwb;
-  C(*R)[MAXM] = Rsh[w];
-  for (int i = lane; i < MAXM * MAXM; i += 32) R[i / MAXM][i % MAXM] = Tr<C>::zero();
-  __syncwarp();
-  const C eps = Tr<C>::eps();
-  const int64_t p0 = gw * npanels / nwt, p1 = (gw + 1) * npanels / nwt;
-  for (int64_t p = p0; p < p1; ++p) {
-    C a[K][MAXM];
-    const int64_t r0 = p * PR;
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-      const int64_t row = r0 + lane + 32 * q;
-      const bool ok = row < rows;
-#pragma unroll
-      for (int k = 0; k < MAXM; ++k)
-        a[q][k] = (ok && k < m) ? ld_as<C>(W[row + (int64_t)k * ld]) : Tr<C>::zero();
-    }
-    for (int j = 0; j < m; ++j) {
-      C pv[K];
-#pragma unroll
-      for (int q = 0; q < K; ++q) pv[q] = Tr<C>::zero();
-#pragma unroll
-      for (int k = 0; k < MAXM; ++k)
-        if (k == j) {
-#pragma unroll
-          for (int q = 0; q < K; ++q) pv[q] = a[q][k];
-        }
-      // Gram row of the pivot column over this warp's panel rows
-      C s[MAXM];
-#pragma unroll
-      for (int k = 0; k < MAXM; ++k) {
-        s[k] = Tr<C>::zero();
-        if (k >= j) {
-          C acc = mul(pv[0], a[0][k]);
-#pragma unroll
-          for (int q = 1; q < K; ++q) acc = fmac(pv[q], a[q][k], acc);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc = add(acc, shfl_xor(acc, o));
-          s[k] = acc;
-        }
-      }
-      // reflector scalars (identical in every lane)
-      C rrow[MAXM];
-#pragma unroll
-      for (int k = 0; k < MAXM; ++k) rrow[k] = (k >= j) ? R[j][k] : Tr<C>::zero();
-      C rjj = Tr<C>::zero();
-#pragma unroll
-      for (int k = 0; k < MAXM; ++k)
-        if (k == j) rjj = rrow[k];
-      __syncwarp();
-      C t = add(fmac(rjj, rjj, s[j]), eps);
-      C alpha = sqrt_(add(t, eps));
-      if (is_pos(rjj)) alpha = neg(alpha);
-      t = fnmac(alpha, rjj, t);
-      const C piv = sub(rjj, alpha);
-      const C tinv = div_(Tr<C>::one(), t);
-#pragma unroll
-      for (int k = 0; k < MAXM; ++k) {
-        if (k > j) {
-          const C c = mul(fmac(piv, rrow[k], s[k]), tinv);
-          if (lane == 0) R[j][k] = fnmac(c, piv, rrow[k]);
-#pragma unroll
-          for (int q = 0; q < K; ++q) a[q][k] = fnmac(c, pv[q], a[q][k]);
-        }
-      }
-      if (lane == 0) R[j][j] = alpha;
-      __syncwarp();
-    }
-  }
-  // stacked output block: rows gw*mb + i (i < mb), columns k < m
-  for (int idx = lane; idx < mb * m; idx += 32) {
-    const int i = idx % mb, k = idx / mb;
-    C v = Tr<C>::zero();
-    if (i < MAXM && i <= k) v = R[i][k];
-    Rout[gw * mb + i + (int64_t)k * ldR] = st_as<RO>(v);
-  }
-}
 
 template <int NCH, class C, class S, class RO>
 __global__ void __launch_bounds__(128)
