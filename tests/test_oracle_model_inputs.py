@@ -62,6 +62,18 @@ def test_philox_known_answers():
         assert tuple(int(x[0]) for x in got) == out
 
 
+def test_uniform_known_answers():
+    # entries 0 and 1 of seed 0 come from block 0, i.e. Philox4x32-10 of counter (0,0,0,0)
+    # under key (0,0), whose published output words are 0x6627E8D5 0xE169C58D 0xBC57AC4C
+    # 0x9B00DBD8; each pair of words (x, y) gives the 53-bit fraction
+    # (floor(x / 2^5) 2^26 + floor(y / 2^6)) / 2^53, evaluated here with exact rationals
+    from fractions import Fraction
+    words = (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)
+    expect = [Fraction((x // 32) * 2 ** 26 + y // 64, 2 ** 53) for x, y in (words[:2], words[2:])]
+    got = uniform_f64(0, 2)
+    assert [Fraction(float(v)) for v in got] == expect
+
+
 def test_uniform_stream_properties():
     a = uniform_f64(7, 10001)
     assert np.all(a >= 0) and np.all(a < 1)

@@ -31,6 +31,17 @@ def test_exact_without_truncation():
         assert rel_err(X, res.cores) <= 1e-12
         assert res.ranks[0] == 1 and res.ranks[-1] == 1
         assert [c.shape[1] for c in res.cores] == list(dims)
+    # with r_max = 1000 the threshold r / f1_min is never reached and Alg. 3 degenerates to
+    # Alg. 1 (k = d); a rank estimate of 8 (threshold 16) makes it combine 2 <= k < d
+    # right-most extents, all different, so the recovery of line 4 runs on a tensor whose
+    # dimension order matters
+    for dims, k in [((2, 3, 4, 3, 2, 5), 3), ((3, 2, 2, 7, 3), 2), ((2, 2, 5, 3, 2, 4), 3)]:
+        X = uniform_tensor(dims, seed=12)
+        res = tt_svd_thick(X, 1000, m_min=16, f1_min=0.5, r_est=8)
+        assert res.k == k and res.m == int(np.prod(dims[len(dims) - k:])), (dims, res.k)
+        assert rel_err(X, res.cores) <= 1e-12, dims
+        assert [c.shape[1] for c in res.cores] == list(dims)
+        assert res.ranks == O.planned_ranks(list(dims), 1000)
 
 
 def test_planted_ranks_are_recovered():

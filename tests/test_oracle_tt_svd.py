@@ -160,6 +160,18 @@ def test_full_contraction_definition():
         assert math.isclose(X[i], v, rel_tol=1e-13, abs_tol=1e-14)
 
 
+def test_planned_ranks_closed_form_and_alg1():
+    # without tolerance truncation r_k = min(r_max, n_1...n_k, n_{k+1}...n_d): the rank of
+    # the k-th unfolding is capped by both of its sides (the maximal TT ranks), then by r_max;
+    # Alg. 1 on a generic tensor reaches exactly these ranks
+    for dims in [(2, 3, 4, 5), (5, 4, 3, 2), (2, 2, 7), (4, 1, 3, 2), (3,), (6, 2), (2, 5, 2, 3, 2)]:
+        d = len(dims)
+        for r_max in (1, 2, 3, 6, 100):
+            closed = [1] + [min(r_max, int(np.prod(dims[:k])), int(np.prod(dims[k:]))) for k in range(1, d)] + [1]
+            assert O.planned_ranks(list(dims), r_max) == closed, (dims, r_max)
+            assert O.tt_svd(uniform_tensor(dims, seed=13), r_max).ranks == closed, (dims, r_max)
+
+
 def test_truncation_rule_hand_cases():
     s = np.array([3.0, 2.0, 1.0])
     # tails after j: j=0:14, j=1:5, j=2:1, j=3:0
@@ -173,6 +185,12 @@ def test_truncation_rule_hand_cases():
     assert list(O.tail_sums(s)) == [14.0, 5.0, 1.0, 0.0]
     assert O.rank_is_ambiguous(s, 1.0, 2)
     assert not O.rank_is_ambiguous(s, math.sqrt(3.0), 2)
+    # a tie on the other side: delta^2 just below the tail after sigma_1 (5) keeps r = 2, but
+    # a sum rounded the other way would take r = 1
+    d_low = math.sqrt(5.0 * (1 - 1e-14))
+    assert O.truncation_rank(s, d_low, 10, 10, 10) == 2
+    assert O.rank_is_ambiguous(s, d_low, 2)
+    assert not O.rank_is_ambiguous(s, math.sqrt(4.0), 2)
 
 
 def test_rank_table_plain():
