@@ -124,6 +124,19 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ---- the metric and the workload, shared by both arms ---------------------------------------
+METRIC = "TT-SVD input GB/s vs 2-read HBM roofline (FP64 form)"
+
+
+def workload_config(n: int, d: int, r_max: int, ranks, world: int) -> dict:
+    """The `config` of the JSON line: the same dict for the CUDA arm and the reference arm."""
+    in_bytes = 8 * n ** d
+    return {"workload": f"TT-SVD of a {n}^{d} FP64 tensor ({in_bytes / 2**30:.0f} GiB), r_max={r_max}, tol=0",
+            "dims": [n] * d, "r_max": r_max, "ranks": list(ranks),
+            "l2_flush": f"input {in_bytes / 2**30:.0f} GiB > L2 (129 MB), no flush",
+            "parallelism": f"{world} independent problem(s), one per GPU"}
+
+
 # ---- CPU oracle throughput ----------------------------------------------------------------
 def cpu_oracle_rate(n: int, r_max: int, seconds: float, seed: int):
     """Times the oracle (Alg. 1, FP64) on a bounded sample: n^8 tensors, repeated."""
@@ -164,10 +177,12 @@ def run_reference(args):
     gbs = X.nbytes / el / 1e9
     cores = len(os.sched_getaffinity(0))
     sample = f"Alg. 1 oracle on a {args.n}^8 uniform FP64 tensor ({X.nbytes / 2**20:.0f} MiB) per step, r_max={args.rmax}"
-    line = {"impl": "reference", "metric": "TT-SVD input GB/s (FP64)", "value": gbs, "unit": "GB/s",
+    config = workload_config(args.n, args.d, args.rmax, O.planned_ranks([args.n] * args.d, args.rmax), args.gpus)
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s",
             "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": el * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"{args.n}^{args.d} FP64 uniform[0,1) TT-SVD, r_max={args.rmax}, tol=0 (sampled as {args.n}^8)"},
+            "data": "synthetic: i.i.d. uniform[0,1) from Philox4x32-10, generated on the host",
+            "config": config,
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -359,14 +374,12 @@ def main():
         extras = run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, stream)
 
     out = {
-        "metric": "TT-SVD input GB/s vs 2-read HBM roofline (FP64 form)",
+        "metric": METRIC,
         "value": value, "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.arith == "f64" else "f64 storage, float-float (2xFP32) arithmetic",
         "data": "synthetic: i.i.d. uniform[0,1) from Philox4x32-10, generated on the device",
-        "config": {"workload": f"TT-SVD of a {args.n}^{args.d} FP64 tensor ({in_bytes / 2**30:.0f} GiB), r_max={args.rmax}, tol=0",
-                   "dims": dims, "r_max": args.rmax, "ranks": ranks, "l2_flush": "input 8 GiB > L2, no flush",
-                   "parallelism": f"{world} independent problem(s), one per GPU"},
+        "config": workload_config(args.n, args.d, args.rmax, ranks, world),
         "two_read_roofline": {"ms": two_read_ms, "frac": two_read_ms / ms, "hbm_gbs": hbm_peak, "source": peak_src},
         "roofline": roof,
         "per_kernel": per_kernel[:8],
