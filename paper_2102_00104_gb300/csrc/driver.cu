@@ -177,7 +177,8 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
     L.kind = 0;
     L.maxm = m_max <= 4 ? 4 : (m_max <= 8 ? 8 : 16);
     // rows per lane 32 / maxm (or 64 / maxm, "tsqr.narrow_k"), 4 CTAs of 4 warps per SM:
-    // measured on GB300 for 2^27 x 8, 12.9 ms against 20.2 ms with 64 / maxm and 2 CTAs
+    // measured on GB300 for 8^10 at r_max = 1 (first step 2^27 x 8), 19.7 ms per TT-SVD
+    // against 20.2 ms with 64 / maxm and 2 CTAs per SM (both without renormalisation)
     L.pr = 32 * ((tune_get("tsqr.narrow_k", 32) == 64 ? 64 : 32) / L.maxm);
     L.smem = 0;
     warps_cap = (int64_t)nsm * tune_get("tsqr.narrow_cpsm", 4) * 4;
