@@ -294,12 +294,37 @@ tt_status tt_profile_read(int max, int* n, int* kinds, int* steps, double* ms, d
 /* Number of kernels this library has launched since it was loaded. */
 tt_status tt_stats(int64_t* launches);
 
-/* Tuning parameters, process-wide (used by the autotuner, paper_2102_00104_gb300/
- * autotune.py).  Keys: "tsqr.cfg.<b>" selects the CTA-cooperative TSQR layout (rows
- * per panel, lanes per column group) for the m-bucket b = 1 (m <= 64), 2 (m <= 80) or
- * 3 (m <= 128) among the alternative layouts 16..20; a layout that cannot hold m is
- * ignored.  value < 0 removes the key.  Results never depend on these settings beyond
- * rounding. */
+/* Tuning parameters, process-wide: kernel and layout choices read when a plan is built
+ * (set by the autotuner, paper_2102_00104_gb300/autotune.py, and by the Python
+ * binding's TT_TUNE="key=value,..." environment variable).  value < 0 removes a key, so
+ * its default applies again.  Results never depend on these settings beyond rounding.
+ * Keys (default in brackets):
+ *   TSQR (Alg. 6 panels, Sec. 3.2)
+ *     "tsqr.col" [1]          column-owned first-level kernel for 16 < m <= 160; 0: row-group kernel
+ *     "tsqr.col.<b>" [1]      the same per m bucket b (0: m <= 32, 1: <= 64, 2: <= 80,
+ *                             3: <= 128, 4: <= 160), float-float form
+ *     "tsqr.colcfg.<b>" [-]   column-owned layout 0..9 (warps, columns per warp, rows per
+ *                             lane) for bucket b; ignored when it cannot hold m
+ *     "tsqr.cols" [1]         shared-memory panel kernel for 160 < m <= 512; 0: row-group kernel
+ *     "tsqr.merge_m" [96]     smallest m whose upper tree levels use the triangle-merge kernel
+ *     "tsqr.pcap_q" [4 or 8]  first-level partial R's at most rows / (q m / 4) when merging
+ *     "tsqr.narrow_k" [32]    narrow kernel (m <= 16): 32 or 64 panel rows per lane x MAXM
+ *     "tsqr.narrow_cpsm" [4]  narrow kernel: CTAs of 4 warps per SM
+ *     "tsqr.narrow_norm" [1]  narrow kernel: renormalise the float-float pairs after each update
+ *   small SVD of R (one-sided Jacobi)
+ *     "svd.block" [1]         block-cyclic cluster Jacobi for m > 48
+ *     "svd.block_nc" [0]      force its cluster size (2..16; other values: cost model)
+ *     "svd.cluster" [1]       ring-ordered cluster Jacobi where the block form does not fit
+ *     "svd.g" [16]            single-CTA Jacobi: lanes per column pair (8, 16 or 32)
+ *     "svd.wide" [1]          wide steps (rows < m): Jacobi on the columns of W^T, no TSQR
+ *     "svd.wide_g" [8..32]    lanes per column pair of the wide Jacobi
+ *   W V_r (Sec. 4.1.2)
+ *     "tsmm.oz" [1]           Ozaki-split tensor-core product: 0 never, 1 where float-float is
+ *                             ALU-bound (m >= 16 and m r >= 6 (m + r)), 2 wherever it applies
+ *     "tsmm.oz_nbuf" [1]      tile buffers per CTA of that kernel (1 or 2)
+ *     "tsmm.tc" [0]           1: the tcgen05 form of the same product where it applies
+ *   batched form
+ *     "batched.streams" [64]  streams of tt_svd_batched (1..128) */
 tt_status tt_tune_set(const char* key, int value);
 
 const char* tt_status_str(tt_status s);

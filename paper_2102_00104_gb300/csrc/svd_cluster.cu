@@ -745,7 +745,10 @@ cudaError_t launch_blk(const void* R, int64_t ldR, const int* m_dev, int m_max, 
 // (measured on GB300 for m = 64, 80, 128, 256 against 2, 4, 8 and 16), falling back to
 // the next size whose four block buffers fit in shared memory; 0 if none does.
 int jacobi_block_plan(Fmt comp, int m_max, int* npl_out) {
-  const int forced = tune_get("svd.block_nc", 0);
+  // "svd.block_nc" forces the cluster size (the block-cyclic order is valid for 2..16 CTAs);
+  // other values are ignored
+  const int forced_nc = tune_get("svd.block_nc", 0);
+  const int forced = forced_nc >= 2 && forced_nc <= 16 ? forced_nc : 0;
   const int pref[4] = {m_max <= 96 ? 4 : 16, m_max <= 96 ? 8 : 8, m_max <= 96 ? 2 : 4, m_max <= 96 ? 16 : 2};
   for (int c = 0; c < 4; ++c) {
     const int nc = forced ? forced : pref[c];
