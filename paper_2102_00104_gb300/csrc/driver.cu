@@ -159,7 +159,7 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
       // tree (m^3 / 6 per pair, log2 P deep) more and shorter first-level panels pay.
       const bool merges = m_max >= tune_get("tsqr.merge_m", 96);
       // rows per CTA >= q4 m / 4 (measured best: m rows for m >= 200, 2 m below)
-      const int64_t q4 = merges ? tune_get("tsqr.pcap_q", m_max >= 200 ? 4 : 8) : 16;
+      const int64_t q4 = merges ? std::max(1, tune_get("tsqr.pcap_q", m_max >= 200 ? 4 : 8)) : 16;
       const int64_t p_cap = std::max<int64_t>(1, 4 * rows / (q4 * (int64_t)m_max));
       ctas = std::min<int64_t>(std::min<int64_t>(L.panels, (int64_t)nsm * cta_per_sm), p_cap);
       if (ctas_override > 0) ctas = std::min<int64_t>(L.panels, ctas_override);
