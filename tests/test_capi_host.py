@@ -100,6 +100,24 @@ def test_tsqr_plans_terminate_for_all_shapes(lib):
                 assert capi.tt_tsqr_query(rows, m, dt) > 0, (rows, m, dt)
 
 
+def test_plans_survive_out_of_range_tuning_values(lib):
+    # tuning keys are user input (TT_TUNE): values outside their range must fall back to a
+    # valid plan, never divide by zero or produce an empty grid
+    odd = {"tsqr.pcap_q": 0, "tsqr.narrow_cpsm": 0, "tsqr.narrow_k": 7, "tsqr.merge_m": 0,
+           "svd.block_nc": 99, "tsqr.colcfg.1": 42, "batched.streams": 0}
+    try:
+        for k, v in odd.items():
+            assert lib.tt_tune_set(k.encode(), v) == capi.TT_OK
+        for m in (1, 8, 16, 17, 64, 100, 200, 400):
+            for rows in (1, 100, 65537, 1 << 24):
+                assert capi.tt_tsqr_query(rows, m, capi.TT_F64) > 0, (rows, m)
+        _, wb = capi.tt_query(10, [8] * 10, 10, 0.0, capi.TT_F64)
+        assert wb > 0
+    finally:
+        for k in odd:
+            lib.tt_tune_set(k.encode(), -1)
+
+
 def test_query_paper_configurations(lib):
     for r in (1, 5, 10, 20, 50):
         _, wb = capi.tt_query(10, [8] * 10, r, 0.0, capi.TT_F64)
