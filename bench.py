@@ -128,6 +128,19 @@ class ClockSampler:
 METRIC = "TT-SVD input GB/s vs 2-read HBM roofline (FP64 form)"
 
 
+# The paper's TT-SVD times for the 8^10 FP64 tensor on one 14-core Skylake socket (Sec. 5.2,
+# the figure of TT-SVD variants on 8^10: the faster of the plain and thick-bounds
+# algorithms), by r_max, in seconds.  Another machine's figure: context for vs_baseline.
+PAPER_TIME_8P10_S = {1: 0.298, 5: 0.611, 10: 0.732, 20: 1.12, 50: 4.23}
+
+
+def paper_input_gbs(n: int, d: int, r_max: int, dtype_bytes: int = 8):
+    """The paper's input GB/s for the same metric and workload, or None when it has none."""
+    if (n, d, dtype_bytes) != (8, 10, 8) or r_max not in PAPER_TIME_8P10_S:
+        return None
+    return dtype_bytes * n ** d / PAPER_TIME_8P10_S[r_max] / 1e9
+
+
 def workload_config(n: int, d: int, r_max: int, ranks, world: int) -> dict:
     """The `config` of the JSON line: the same dict for the CUDA arm and the reference arm."""
     in_bytes = 8 * n ** d
@@ -376,7 +389,13 @@ def main():
     out = {
         "metric": METRIC,
         "value": value, "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": (value / paper_input_gbs(args.n, args.d, args.rmax)
+                        if paper_input_gbs(args.n, args.d, args.rmax) else None),
+        "vs_baseline_ref": ({"gbs": paper_input_gbs(args.n, args.d, args.rmax),
+                             "source": "the paper's TT-SVD time for this tensor and r_max on one 14-core "
+                                       "Skylake socket (Sec. 5.2), another machine: context, not the target"}
+                            if paper_input_gbs(args.n, args.d, args.rmax) else None),
         "dtype": "f64" if args.arith == "f64" else "f64 storage, float-float (2xFP32) arithmetic",
         "data": "synthetic: i.i.d. uniform[0,1) from Philox4x32-10, generated on the device",
         "config": workload_config(args.n, args.d, args.rmax, ranks, world),

@@ -48,3 +48,15 @@ def test_reference_other_ranks_exit_quietly():
     p = run({"RANK": "1", "WORLD_SIZE": "2"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_paper_figure_for_vs_baseline():
+    # 8^10 FP64 = 8.59 GB; the paper's 0.732 s at r_max = 10 is 11.7 GB/s of input
+    bench = load_bench()
+    assert abs(bench.paper_input_gbs(8, 10, 10) - 8 * 8 ** 10 / 0.732 / 1e9) < 1e-9
+    assert round(bench.paper_input_gbs(8, 10, 10), 1) == 11.7
+    assert round(bench.paper_input_gbs(8, 10, 1), 1) == 28.8
+    # no figure for other workloads or for the FP32 form
+    assert bench.paper_input_gbs(4, 10, 8) is None
+    assert bench.paper_input_gbs(8, 10, 32) is None
+    assert bench.paper_input_gbs(8, 10, 10, dtype_bytes=4) is None
