@@ -181,7 +181,7 @@ def run_reference(args):
     from paper_2102_00104_gb300.inputs import uniform_tensor
     dims = (args.n,) * 8
     X = uniform_tensor(dims, seed=args.seed)
-    for _ in range(min(W, 1)):
+    for _ in range(W):
         O.tt_svd(X, args.rmax)
     t0 = time.perf_counter()
     for _ in range(K):
