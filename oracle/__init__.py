@@ -30,5 +30,6 @@ Modules
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, library routines, brute force or values printed in the
-paper; none is "parity unpinned".
+paper; none is "parity unpinned".  ``tests/test_oracle_mutants.py`` plants one
+plausible mistake at a time in a copy of these modules and checks that a pin fails.
 """
