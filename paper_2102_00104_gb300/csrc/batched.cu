@@ -162,6 +162,7 @@ struct tt_server {
     int slot = -1;
     tt_job_result res{};
     bool done = false;
+    cudaEvent_t ready = nullptr;  // recorded on the submitter's stream: inputs and outputs ready
   };
   size_t budget = 0, arena_bytes = 0, accounted = 0;
   double timeout_s = 60.0;
@@ -170,6 +171,7 @@ struct tt_server {
   std::vector<cudaStream_t> slot_stream;
   std::vector<cudaEvent_t> slot_event;
   std::vector<uint64_t> slot_ticket;                 // 0 = free
+  std::vector<cudaEvent_t> spare_events;             // recycled ready events
   std::map<uint64_t, Req> reqs;
   std::deque<uint64_t> queue;
   uint64_t next_ticket = 1;
@@ -228,6 +230,7 @@ struct tt_server {
                                                  : TT_ENUMERIC;
       }
       r.done = true;
+      if (r.ready) { spare_events.push_back(r.ready); r.ready = nullptr; }
       arena_free(r.arena_off, r.ws);
       accounted -= r.acct;
       slot_ticket[k] = 0;
@@ -248,7 +251,10 @@ struct tt_server {
       r.res.t_start = now_s();
       accounted += r.acct;
       slot_ticket[slot] = r.ticket;
-      tt_status st = run_job(r.job, arena + off, r.ws, slot_stream[slot]);
+      // the job's kernels start only after the submitter's stream has reached the submit
+      tt_status st = TT_OK;
+      if (r.ready && cudaStreamWaitEvent(slot_stream[slot], r.ready, 0) != cudaSuccess) st = TT_ECUDA;
+      if (st == TT_OK) st = run_job(r.job, arena + off, r.ws, slot_stream[slot]);
       if (st != TT_OK) r.res.status = st;
       cudaEventRecord(slot_event[slot], slot_stream[slot]);
     }
@@ -314,7 +320,7 @@ tt_status tt_serve_create(size_t hbm_budget_bytes, const tt_serve_opts* opts, tt
   return TT_OK;
 }
 
-tt_status tt_serve_submit(tt_server* s, const tt_job* job, uint64_t* ticket) {
+tt_status tt_serve_submit(tt_server* s, const tt_job* job, void* ready_stream, uint64_t* ticket) {
   if (!s || !job || !ticket) return TT_EINVAL;
   size_t ws = 0;
   tt_status st = job_work_bytes(*job, &ws);
@@ -323,7 +329,22 @@ tt_status tt_serve_submit(tt_server* s, const tt_job* job, uint64_t* ticket) {
   if (acct > s->budget || ((ws + 255) & ~(size_t)255) > s->arena_bytes) return TT_ENOMEM;
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) return TT_ECANCELLED;
+  // mark the point of the submitter's stream after which the inputs and outputs are ready
+  cudaEvent_t ready = nullptr;
+  if (!s->spare_events.empty()) {
+    ready = s->spare_events.back();
+    s->spare_events.pop_back();
+  } else if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) {
+    set_last_error_text("tt_serve_submit: cudaEventCreateWithFlags failed");
+    return TT_ECUDA;
+  }
+  if (cudaEventRecord(ready, (cudaStream_t)ready_stream) != cudaSuccess) {
+    s->spare_events.push_back(ready);
+    set_last_error_text("tt_serve_submit: cudaEventRecord on the ready stream failed");
+    return TT_ECUDA;
+  }
   tt_server::Req r;
+  r.ready = ready;
   r.ticket = s->next_ticket++;
   r.job = *job;
   r.ws = ws;
@@ -357,6 +378,16 @@ tt_status tt_serve_poll(tt_server* s, uint64_t ticket, int wait, tt_job_result* 
   return TT_OK;
 }
 
+tt_status tt_serve_release(tt_server* s, uint64_t ticket) {
+  if (!s) return TT_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return TT_EINVAL;
+  if (!it->second.done) return TT_EAGAIN;
+  s->reqs.erase(it);
+  return TT_OK;
+}
+
 tt_status tt_serve_destroy(tt_server* s) {
   if (!s) return TT_EINVAL;
   {
@@ -367,6 +398,7 @@ tt_status tt_serve_destroy(tt_server* s) {
       r.res.status = TT_ECANCELLED;
       r.res.t_done = now_s();
       r.done = true;
+      if (r.ready) { s->spare_events.push_back(r.ready); r.ready = nullptr; }
     }
     s->queue.clear();
     s->cv.notify_all();
@@ -388,6 +420,9 @@ tt_status tt_serve_destroy(tt_server* s) {
       cudaStreamDestroy(s->slot_stream[k]);
       cudaEventDestroy(s->slot_event[k]);
     }
+    for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
+    for (auto& kv : s->reqs)
+      if (kv.second.ready) cudaEventDestroy(kv.second.ready);
     cudaFree(s->arena);
     delete s;
   }

@@ -122,15 +122,60 @@ def test_serve_same_alone_and_in_mix():
     srv = capi.tt_serve_create(8 << 30, max_inflight=6)
     try:
         jobs, tickets = [], []
-        for dims, dt, r, X, tol in mixed:
+        # the first half is queued at once; the second half arrives while the first runs
+        for k, (dims, dt, r, X, tol) in enumerate(mixed):
+            if k == len(mixed) // 2:
+                code, res = capi.tt_serve_poll(srv, tickets[0], wait=True)
+                assert code == capi.TT_OK
             j = api.Job(fortran_flat(X, dt), dims, r, tol)
             jobs.append(j)
-            tickets.append(capi.tt_serve_submit(srv, j.c))
+            tickets.append(api.serve_submit(srv, j))
+        spans = []
         for t, j, ref in zip(tickets, jobs, alone):
             code, res = capi.tt_serve_poll(srv, t, wait=True)
             assert code == capi.TT_OK and res.status == capi.TT_OK
             assert res.t_submit <= res.t_start <= res.t_done
+            spans.append((res.t_start, res.t_done))
             same_result(j.result(), ref)
+        # continuous batching: requests ran on the device at the same time, and some of
+        # the later arrivals were admitted while earlier requests were still running
+        overlaps = sum(1 for a in range(len(spans)) for b in range(a + 1, len(spans))
+                       if spans[a][0] < spans[b][1] and spans[b][0] < spans[a][1])
+        assert overlaps >= 1
+        late = spans[len(spans) // 2:]
+        early = spans[:len(spans) // 2]
+        assert any(s0 < max(d for _, d in early) for s0, _ in late)
+        # finished requests can be released; a released ticket is unknown afterwards
+        for t in tickets:
+            assert capi.tt_serve_release(srv, t) == capi.TT_OK
+            assert capi.tt_serve_poll(srv, t, wait=False)[0] == capi.TT_EINVAL
+            assert capi.tt_serve_release(srv, t) == capi.TT_EINVAL
+    finally:
+        capi.tt_serve_destroy(srv)
+
+
+def test_serve_waits_for_the_submitters_stream():
+    """The input is written on a side stream that is still busy at submission; the
+    request must read the written values, and its zeroed outputs must not be cleared
+    again after it ran."""
+    dims = (4,) * 7
+    X = uniform_tensor(dims, seed=21)
+    ref = single(dims, torch.float64, 8, X)
+    Xd = torch.zeros(X.size, dtype=torch.float64, device="cuda")
+    src = fortran_flat(X)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    srv = capi.tt_serve_create(2 << 30, max_inflight=2)
+    try:
+        with torch.cuda.stream(side):
+            torch.cuda._sleep(50_000_000)          # keeps the side stream busy for ~25 ms
+            Xd.copy_(src)
+            job = api.Job(Xd, dims, 8)             # outputs cleared on the side stream too
+            t = api.serve_submit(srv, job, side)
+        code, res = capi.tt_serve_poll(srv, t, wait=True)
+        assert code == capi.TT_OK and res.status == capi.TT_OK
+        side.synchronize()
+        same_result(job.result(), ref)
     finally:
         capi.tt_serve_destroy(srv)
 
@@ -145,7 +190,7 @@ def test_serve_admission_under_budget_and_cancel():
     srv = capi.tt_serve_create(int(per_req * 1.5), max_inflight=4, arena_bytes=int(wb * 1.5) + 4096)
     try:
         jobs = [api.Job(X, dims, 16) for _ in range(5)]
-        tickets = [capi.tt_serve_submit(srv, j.c) for j in jobs]
+        tickets = [api.serve_submit(srv, j) for j in jobs]
         code, _ = capi.tt_serve_poll(srv, tickets[-1], wait=False)
         assert code in (capi.TT_EAGAIN, capi.TT_OK)
         starts = []
@@ -162,13 +207,13 @@ def test_serve_admission_under_budget_and_cancel():
         # a request that can never fit the budget is refused at submission
         Xbig = torch.zeros(8 ** 8, dtype=torch.float64, device="cuda")
         with pytest.raises(capi.TTError):
-            capi.tt_serve_submit(srv, api.Job(Xbig, (8,) * 8, 16).c)
+            api.serve_submit(srv, api.Job(Xbig, (8,) * 8, 16))
     finally:
         capi.tt_serve_destroy(srv)
     # stopping a server with queued requests cancels them and returns promptly
     srv = capi.tt_serve_create(int(per_req * 1.5), max_inflight=1, arena_bytes=int(wb * 1.5) + 4096)
     jobs = [api.Job(X, dims, 16) for _ in range(6)]
-    tickets = [capi.tt_serve_submit(srv, j.c) for j in jobs]
+    tickets = [api.serve_submit(srv, j) for j in jobs]
     t0 = time.time()
     assert capi.lib().tt_serve_destroy(srv) == capi.TT_OK
     assert time.time() - t0 < 30
