@@ -13,6 +13,7 @@
 // the working arithmetic, so each rotation is orthogonal to working precision
 // even though its angle is only FP32-accurate (the next sweep removes the
 // remaining small coupling).
+#include <cstdio>
 #include <mutex>
 
 #include "tsqr_col.cuh"
@@ -123,7 +124,7 @@ k_jacobi(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, i
   for (int idx = tid; idx < ldA * mp; idx += nt) {
     const int i = idx % ldA, k = idx / ldA;
     C a = Tr<C>::zero();
-    if (i < m && k < m && i <= k) a = scale_pow2<C>(ld_as<C>(R[i + (int64_t)k * ldR]), -ex);
+    if (i < m && k < m && i <= k) a = flush_tiny(scale_pow2<C>(ld_as<C>(R[i + (int64_t)k * ldR]), -ex));
     A[idx] = a;
     V[idx] = (i == k) ? Tr<C>::one() : Tr<C>::zero();
   }
@@ -302,7 +303,7 @@ k_jacobi_wide(const WI* __restrict__ W, int64_t ldW, int rows, const int* __rest
   for (int idx = tid; idx < ncp * m; idx += nt) {
     const int p = idx % ncp, i = idx / ncp;
     A[i + (size_t)p * lda] =
-        p < nc ? scale_pow2<C>(ld_as<C>(W[p + (int64_t)i * ldW]), -ex) : Tr<C>::zero();
+        p < nc ? flush_tiny(scale_pow2<C>(ld_as<C>(W[p + (int64_t)i * ldW]), -ex)) : Tr<C>::zero();
   }
   __syncthreads();
   float fro = 0.f;
@@ -525,7 +526,8 @@ __global__ void k_truncate(const double* __restrict__ sigma, int64_t rows, int s
   st->err2 += disc;
   st->r[step_i - 1] = r;
   st->m[step_i - 1] = n_next * r;
-  if (sigma_out) for (int k = 0; k < s; ++k) sigma_out[k] = sigma[k];
+  // sigma of X itself: the unfoldings were read as X 2^-k (exact power of two)
+  if (sigma_out) for (int k = 0; k < s; ++k) sigma_out[k] = ldexp(sigma[k], st->xr.k);
   if (ranks_out) ranks_out[step_i - 1] = r;
 }
 
@@ -548,24 +550,28 @@ __global__ void k_set_rank(DevState* st, int step_i, int n_next, int r) {
   st->m[step_i - 1] = n_next * r;
 }
 
+// dst = src as FP64, times 2^xr->k when xr is given (a result of an input read as X 2^-k)
 template <class S>
 __global__ void k_copy_mat_f64(const S* __restrict__ src, int64_t lds, int rows, int cols,
-                               int upper, double* __restrict__ dst, int64_t ldd) {
+                               int upper, double* __restrict__ dst, int64_t ldd, const XRange* xr) {
+  const int k2 = xr ? xr->k : 0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)rows * cols;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx % rows), k = (int)(idx / rows);
-    double v = to_f64(ld_as<df>(src[i + k * lds]));
+    double v = ldexp(to_f64(ld_as<df>(src[i + k * lds])), k2);
     if (upper && i > k) v = 0.0;
     dst[i + k * ldd] = v;
   }
 }
 template <>
 __global__ void k_copy_mat_f64<double>(const double* __restrict__ src, int64_t lds, int rows,
-                                       int cols, int upper, double* __restrict__ dst, int64_t ldd) {
+                                       int cols, int upper, double* __restrict__ dst, int64_t ldd,
+                                       const XRange* xr) {
+  const int k2 = xr ? xr->k : 0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)rows * cols;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx % rows), k = (int)(idx / rows);
-    double v = src[i + k * lds];
+    double v = ldexp(src[i + k * lds], k2);
     if (upper && i > k) v = 0.0;
     dst[i + k * ldd] = v;
   }
@@ -578,16 +584,45 @@ __global__ void k_core_identity(int m, double* core) {
 }
 
 template <class S>
-__global__ void k_to_f64(const S* __restrict__ src, int64_t count, double* __restrict__ dst) {
+__global__ void k_to_f64(const S* __restrict__ src, int64_t count, double* __restrict__ dst,
+                         const XRange* xr) {
+  const int k2 = xr ? xr->k : 0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < count;
        idx += (int64_t)gridDim.x * blockDim.x)
-    dst[idx] = to_f64(ld_as<df>(src[idx]));
+    dst[idx] = ldexp(to_f64(ld_as<df>(src[idx])), k2);
 }
 template <>
-__global__ void k_to_f64<double>(const double* __restrict__ src, int64_t count, double* __restrict__ dst) {
+__global__ void k_to_f64<double>(const double* __restrict__ src, int64_t count, double* __restrict__ dst,
+                                 const XRange* xr) {
+  const int k2 = xr ? xr->k : 0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < count;
        idx += (int64_t)gridDim.x * blockDim.x)
-    dst[idx] = src[idx];
+    dst[idx] = ldexp(src[idx], k2);
+}
+
+// largest encoded exponent of a strided sample of X (at most 64 Ki entries, spread over
+// the whole tensor so that column and block scales are seen): one atomic per warp
+template <class S>
+__global__ void k_range_sample(const S* __restrict__ X, int64_t count, int64_t nsample,
+                               XRange* xr) {
+  int e = 0;
+  const int64_t stride = count / nsample;  // >= 1: nsample <= count
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nsample;
+       j += (int64_t)gridDim.x * blockDim.x)
+    e = max(e, expo_enc(X[j * stride]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0 && e) atomicMax(&xr->sample, e);
+}
+
+// after the first pass of the first TSQR level: keep its shift, or run it again with the
+// shift of the largest magnitude it met
+__global__ void k_range_decide(XRange* xr) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k_try = xr_shift_for(xr->sample);
+  const bool redo = xr_needs_redo(k_try, xr->seen);
+  xr->redo = redo ? 1 : 0;
+  xr->k = redo ? xr_shift_for(xr->seen) : k_try;
 }
 
 __global__ void k_fill_nan(double* dst, int64_t count) {
@@ -604,6 +639,7 @@ struct InitArgs {
 __global__ void k_init_state(DevState* st, InitArgs a) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   st->status = 0;
+  st->xr = XRange{0, 0, 0, 0};
   st->first_done = 0;
   st->delta2 = 0.0;
   st->err2 = 0.0;
@@ -618,7 +654,7 @@ __global__ void k_finish(const DevState* st, int d, int64_t* ranks_out, double* 
     ranks_out[d] = 1;
     for (int i = 1; i < d; ++i) ranks_out[i] = st->r[i];
   }
-  if (err2_out) *err2_out = st->err2;
+  if (err2_out) *err2_out = ldexp(st->err2, 2 * st->xr.k);
 }
 
 inline unsigned grid_for(int64_t n, int bs) {
@@ -795,11 +831,11 @@ cudaError_t launch_set_rank(DevState* st, int step_i, int n_next, int r, cudaStr
 }
 
 cudaError_t launch_copy_mat_f64(Fmt f, const void* src, int64_t lds, int rows, int cols, int upper,
-                                double* dst, int64_t ldd, cudaStream_t s) {
+                                double* dst, int64_t ldd, cudaStream_t s, const XRange* xr) {
   const unsigned g = grid_for((int64_t)rows * cols, 256);
-  if (f == Fmt::F64) k_copy_mat_f64<double><<<g, 256, 0, s>>>((const double*)src, lds, rows, cols, upper, dst, ldd);
-  else if (f == Fmt::DF) k_copy_mat_f64<df><<<g, 256, 0, s>>>((const df*)src, lds, rows, cols, upper, dst, ldd);
-  else k_copy_mat_f64<float><<<g, 256, 0, s>>>((const float*)src, lds, rows, cols, upper, dst, ldd);
+  if (f == Fmt::F64) k_copy_mat_f64<double><<<g, 256, 0, s>>>((const double*)src, lds, rows, cols, upper, dst, ldd, xr);
+  else if (f == Fmt::DF) k_copy_mat_f64<df><<<g, 256, 0, s>>>((const df*)src, lds, rows, cols, upper, dst, ldd, xr);
+  else k_copy_mat_f64<float><<<g, 256, 0, s>>>((const float*)src, lds, rows, cols, upper, dst, ldd, xr);
   return cudaGetLastError();
 }
 
@@ -822,12 +858,38 @@ cudaError_t launch_join_ranks(const int64_t* r1, int p, const int64_t* r2, int q
 }
 
 cudaError_t launch_convert_to_f64(Fmt f, const void* src, int64_t count, double* dst,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, const XRange* xr) {
   if (count <= 0) return cudaSuccess;
   const unsigned g = grid_for(count, 256);
-  if (f == Fmt::F64) k_to_f64<double><<<g, 256, 0, s>>>((const double*)src, count, dst);
-  else if (f == Fmt::DF) k_to_f64<df><<<g, 256, 0, s>>>((const df*)src, count, dst);
-  else k_to_f64<float><<<g, 256, 0, s>>>((const float*)src, count, dst);
+  if (f == Fmt::F64) k_to_f64<double><<<g, 256, 0, s>>>((const double*)src, count, dst, xr);
+  else if (f == Fmt::DF) k_to_f64<df><<<g, 256, 0, s>>>((const df*)src, count, dst, xr);
+  else k_to_f64<float><<<g, 256, 0, s>>>((const float*)src, count, dst, xr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_range_sample(Fmt f, const void* X, int64_t count, XRange* xr, cudaStream_t s) {
+  if (f != Fmt::F64 && f != Fmt::F32) return cudaErrorInvalidValue;
+  if (count <= 0) return cudaSuccess;
+  const int64_t ns = count < 65536 ? count : 65536;
+  const unsigned g = grid_for(ns, 256) < 64 ? grid_for(ns, 256) : 64;
+  if (f == Fmt::F64)
+    k_range_sample<double><<<g, 256, 0, s>>>(static_cast<const double*>(X), count, ns, xr);
+  else
+    k_range_sample<float><<<g, 256, 0, s>>>(static_cast<const float*>(X), count, ns, xr);
+  return cudaGetLastError();
+}
+
+__global__ void k_range_set_sample(XRange* xr, int enc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) xr->sample = enc;
+}
+
+cudaError_t launch_range_set_sample(XRange* xr, int enc, cudaStream_t s) {
+  k_range_set_sample<<<1, 32, 0, s>>>(xr, enc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_range_decide(XRange* xr, cudaStream_t s) {
+  k_range_decide<<<1, 32, 0, s>>>(xr);
   return cudaGetLastError();
 }
 
@@ -886,10 +948,12 @@ cudaError_t noalloc_scratch(void** out) {
   return cudaSuccess;
 }
 
-// a sweep limit or a non-finite value leaves a nonzero status: report it as sigma[0] = NaN
-__global__ void k_noalloc_mark(const int* status, double* sigma) {
-  if (threadIdx.x == 0 && blockIdx.x == 0 && *status != 0)
-    sigma[0] = __longlong_as_double(0x7FF8000000000000ll);
+// a sweep limit or a non-finite value (a status bit, or a sigma that is not finite):
+// report it as sigma[0] = NaN
+__global__ void k_noalloc_mark(const int* status, double* sigma, int m) {
+  bool bad = *status != 0;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) bad |= !isfinite(sigma[k]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) sigma[0] = __longlong_as_double(0x7FF8000000000000ll);
 }
 }  // namespace
 
@@ -907,7 +971,9 @@ extern "C" tt_status tt_small_svd_noalloc(const double* R, int m, double* sigma,
   void* base = nullptr;
   cudaError_t e = noalloc_scratch(&base);
   if (e != cudaSuccess) {
-    set_last_error_text(cudaGetErrorString(e));
+    char buf[192];
+    snprintf(buf, sizeof(buf), "tt_small_svd_noalloc: scratch address lookup: %s", cudaGetErrorString(e));
+    set_last_error_text(buf);
     return TT_ECUDA;
   }
   const int mp = m + (m & 1);
@@ -918,11 +984,20 @@ extern "C" tt_status tt_small_svd_noalloc(const double* R, int m, double* sigma,
   df* Vres = Vw + kNoAllocDf;
   // the status word keeps the previous call's value: clear it; A, V and the result are
   // written in full by the kernels before they are read
-  if ((e = cudaMemsetAsync(status, 0, sizeof(int), s)) != cudaSuccess) return TT_ECUDA;
+  auto fail = [](const char* what, cudaError_t err) {
+    char buf[192];
+    snprintf(buf, sizeof(buf), "tt_small_svd_noalloc: %s: %s", what, cudaGetErrorString(err));
+    set_last_error_text(buf);
+    return TT_ECUDA;
+  };
+  if ((e = cudaMemsetAsync(status, 0, sizeof(int), s)) != cudaSuccess)
+    return fail("clearing the status word", e);
   if ((e = launch_jacobi(Fmt::DF, Fmt::F64, R, m, nullptr, m, A, Vw, mp, sigma, Vres, mp, status,
                          nullptr, s)) != cudaSuccess)
-    return TT_ECUDA;
-  if ((e = launch_copy_mat_f64(Fmt::DF, Vres, mp, m, m, 0, V, m, s)) != cudaSuccess) return TT_ECUDA;
-  k_noalloc_mark<<<1, 32, 0, s>>>(status, sigma);
-  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ECUDA;
+    return fail("Jacobi launch", e);
+  if ((e = launch_copy_mat_f64(Fmt::DF, Vres, mp, m, m, 0, V, m, s)) != cudaSuccess)
+    return fail("copy of V", e);
+  k_noalloc_mark<<<1, 256, 0, s>>>(status, sigma, m);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail("status mark launch", e);
+  return TT_OK;
 }

@@ -49,6 +49,34 @@ def test_noalloc_matches_workspace_entry_point_twice():
         assert np.max(np.abs(V * signs - ref_V)) <= 1e-12 * max(m, 10)
 
 
+def test_noalloc_at_its_size_limit_against_lapack():
+    ensure_lib()
+    # m = 256 fills the Jacobi working copies of the static scratch exactly; 255 is odd
+    for m, seed in ((256, 3), (255, 4)):
+        R = graded_r(m, seed)
+        ref = np.linalg.svd(R, compute_uv=False)
+        for _ in range(2):
+            sig, V = noalloc_svd(R)
+            assert np.max(np.abs(sig - ref)) <= 1e-12 * ref[0]
+            assert np.max(np.abs(V.T @ V - np.eye(m))) <= 1e-13 * m
+            # R V has orthogonal columns of norms sigma
+            assert np.max(np.abs(np.linalg.norm(R @ V, axis=0) - sig)) <= 1e-12 * ref[0]
+
+
+def test_noalloc_reports_a_device_failure_as_nan():
+    ensure_lib()
+    # a non-finite entry cannot give finite singular values: the kernels finish (the
+    # Jacobi sweeps are bounded) and the failure shows as sigma[0] = NaN
+    R = graded_r(40, 5)
+    R[3, 7] = np.nan
+    sig, _ = noalloc_svd(R)
+    assert np.isnan(sig[0])
+    # the next call on a finite matrix is unaffected (the status word is cleared)
+    R = graded_r(40, 6)
+    sig, _ = noalloc_svd(R)
+    assert np.max(np.abs(sig - np.linalg.svd(R, compute_uv=False))) <= 1e-12 * sig[0]
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     ensure_lib()
     L = capi.lib()
