@@ -130,7 +130,12 @@ tt_status tt_core_caps(int d, const int64_t* n, int r_max, int64_t* caps,
  * Step elision: when tol == 0 and min(r_max, rows_i) >= n_i r_i, V would be a
  * square orthogonal matrix; the step is skipped (core = identity, W^(i-1) is a
  * view of W^(i)).  Ranks, later singular values and the approximation are
- * unchanged; only the gauge of that core differs.  opts->no_elide disables it. */
+ * unchanged; only the gauge of that core differs.  opts->no_elide disables it.
+ * Range: any finite X.  In the float-float and FP32 arithmetics (FP32's exponent range) X
+ * is read as X 2^-k with k from its largest magnitude (tt_range_rule), and sigma_out,
+ * err2_out and the core that carries the norm are scaled back by 2^k, 2^2k and 2^k;
+ * results are correct wherever they are representable in FP64 (err2 of a tensor whose
+ * squared norm is below DBL_MIN underflows). */
 tt_status tt_svd(const void* X, tt_dtype dt, int d, const int64_t* n, int r_max, double tol,
                  double* const* cores_out, int64_t* ranks_out, double* sigma_out,
                  double* err2_out, void* work, size_t work_bytes, void* stream);
@@ -267,12 +272,22 @@ typedef struct {
 } tt_job_result;
 
 tt_status tt_serve_create(size_t hbm_budget_bytes, const tt_serve_opts* opts, tt_server** out);
-/* Queue a request (copied); returns TT_ENOMEM if it can never fit the budget or arena. */
-tt_status tt_serve_submit(tt_server* s, const tt_job* job, uint64_t* ticket);
+/* Queue a request (the tt_job is copied); returns TT_ENOMEM if it can never fit the
+ * budget or arena.  ready_stream: the caller's stream (cudaStream_t as void*, NULL = the
+ * legacy default stream) on which the request's input and output buffers are written
+ * or cleared; the server records an event on it at submission, and the request's kernels
+ * wait for that event, so work queued on ready_stream before the submit is complete
+ * before the request reads X or writes its outputs.  Work queued later on ready_stream
+ * is not ordered with the request: poll until it is done before touching its buffers. */
+tt_status tt_serve_submit(tt_server* s, const tt_job* job, void* ready_stream, uint64_t* ticket);
 /* TT_OK with *out filled when the request is done; TT_EAGAIN if not yet (wait = 0);
  * with wait != 0 blocks up to timeout_s, then TT_ETIMEOUT.  A finished ticket may be
- * polled again. */
+ * polled again until it is released. */
 tt_status tt_serve_poll(tt_server* s, uint64_t ticket, int wait, tt_job_result* out);
+/* Forget a finished request (its result can no longer be polled), so that a long-running
+ * server keeps no record per past request.  TT_EAGAIN if it has not finished, TT_EINVAL
+ * for an unknown or already released ticket. */
+tt_status tt_serve_release(tt_server* s, uint64_t ticket);
 /* Stops admission, cancels queued requests (TT_ECANCELLED), waits (bounded) for
  * running ones, frees the arena and streams. */
 tt_status tt_serve_destroy(tt_server* s);
@@ -283,13 +298,21 @@ tt_status tt_serve_destroy(tt_server* s);
  * and flops; tt_profile(0) stops; both clear earlier records.  tt_profile_read
  * synchronises the recorded events and returns up to `max` records:
  * kinds[k] (0 TSQR first level, 1 TSQR upper levels, 2 SVD of R, 3 rank choice
- * and core, 4 W*V_r), steps[k] (the step index i), ms[k], bytes[k], flops[k],
+ * and core, 4 W*V_r, 5 the exponent-range decision and the re-run of the first level
+ * that it may ask for), steps[k] (the step index i), ms[k], bytes[k], flops[k],
  * info[k] (Jacobi sweeps for kind 2 -- valid while the workspace of that call is
  * untouched -- else -1).  *n receives the number of records available.  Any
  * output array may be NULL. */
 tt_status tt_profile(int enable);
 tt_status tt_profile_read(int max, int* n, int* kinds, int* steps, double* ms, double* bytes,
                           double* flops, int* info);
+
+/* Arithmetic peak of this GPU, measured: kind 0 = FP32 FMA, 1 = FP64 FMA, 2 = the lazy
+ * float-float multiply-add of the float-float dot products (one FP64-equivalent FMA).
+ * *flops_per_s = 2 x multiply-adds per second over every SM (8 CTAs of 256 threads per
+ * SM, 8 independent chains per thread, a warm-up run, then one timed run of ~10 ms with
+ * CUDA events on `stream`).  Synchronises `stream`.  TT_EINVAL for another kind. */
+tt_status tt_fma_rate(int kind, double* flops_per_s, void* stream);
 
 /* Number of kernels this library has launched since it was loaded. */
 tt_status tt_stats(int64_t* launches);
@@ -326,6 +349,19 @@ tt_status tt_stats(int64_t* launches);
  *   batched form
  *     "batched.streams" [64]  streams of tt_svd_batched (1..128) */
 tt_status tt_tune_set(const char* key, int value);
+
+/* The exponent-range rule of the FP64 form in float-float arithmetic, for tests.
+ * Float-float has FP32's exponent range, so tt_svd reads an FP64 X as X 2^-k (k an exact
+ * power-of-two shift) and scales sigma_out, err2_out and the core that carries the norm
+ * back by 2^k; entries below 2^-62 times the largest one are read as zero (their squares
+ * would leave FP32's range), which changes no singular value by more than
+ * 2^-62 sqrt(n_1...n_d) max|x| (2^-47 max|x| for 2^30 entries).  Arguments:
+ * floor(log2 max|x|) of a strided sample of X and of all of X (what the first TSQR
+ * level, Alg. 2 line 5, meets), TT_RANGE_NONE when nothing nonzero and finite was seen.
+ * Outputs: the shift of the first pass (*k_try), whether that level runs again (*redo),
+ * and the shift every later step and the results use (*k).  Pure host computation. */
+#define TT_RANGE_NONE (-100000)
+tt_status tt_range_rule(int sample_exp, int seen_exp, int* k_try, int* redo, int* k);
 
 const char* tt_status_str(tt_status s);
 

@@ -236,6 +236,12 @@ class Job:
         return TTResult(cores=cores, ranks=r, err2=float(self.err2.item()))
 
 
+def serve_submit(srv, job: "Job", stream=None) -> int:
+    """Queue a Job on a tt_serve server, ordered after the work queued so far on the
+    stream (torch's current stream by default) that filled its input and cleared its outputs."""
+    return capi.tt_serve_submit(srv, job.c, _stream_ptr(stream))
+
+
 def svd_batched(jobs, stream=None):
     """Runs tt_svd_batched over Job objects (asynchronous on the stream); returns the workspace."""
     cj = [j.c for j in jobs]

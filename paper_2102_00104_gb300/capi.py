@@ -24,9 +24,9 @@ TT_ARITH_AUTO, TT_ARITH_DF, TT_ARITH_F64 = 0, 1, 2
 EXPORTED = ["tt_query", "tt_core_caps", "tt_svd", "tt_svd_ex", "tt_last_device_status",
             "tt_tsqr_query", "tt_tsqr", "tt_small_svd_query", "tt_small_svd", "tt_tsmm",
             "tt_gen_uniform", "tt_batched_query", "tt_svd_batched", "tt_serve_create",
-            "tt_serve_submit", "tt_serve_poll", "tt_serve_destroy", "tt_status_str",
+            "tt_serve_submit", "tt_serve_poll", "tt_serve_release", "tt_serve_destroy", "tt_status_str",
             "tt_profile", "tt_profile_read", "tt_stats", "tt_last_error", "tt_small_svd_noalloc", "tt_tune_set",
-            "tt_query_from_host", "tt_svd_from_host", "tt_query_ex"]
+            "tt_query_from_host", "tt_svd_from_host", "tt_query_ex", "tt_range_rule", "tt_fma_rate"]
 
 
 class tt_opts(C.Structure):
@@ -87,8 +87,9 @@ _SIGS = {
     "tt_batched_query": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
     "tt_svd_batched": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "tt_serve_create": (C.c_int, [C.c_size_t, C.c_void_p, C.c_void_p]),
-    "tt_serve_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tt_serve_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tt_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.c_void_p]),
+    "tt_serve_release": (C.c_int, [C.c_void_p, C.c_uint64]),
     "tt_serve_destroy": (C.c_int, [C.c_void_p]),
     "tt_status_str": (C.c_char_p, [C.c_int]),
     "tt_profile": (C.c_int, [C.c_int]),
@@ -98,6 +99,8 @@ _SIGS = {
     "tt_last_error": (C.c_char_p, []),
     "tt_small_svd_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tt_tune_set": (C.c_int, [C.c_char_p, C.c_int]),
+    "tt_range_rule": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tt_fma_rate": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -227,7 +230,8 @@ def tt_status_str(code):
     return lib().tt_status_str(code).decode()
 
 
-PROFILE_KINDS = {0: "tsqr_first_level", 1: "tsqr_upper_levels", 2: "svd_of_R", 3: "rank_and_core", 4: "tsmm"}
+PROFILE_KINDS = {0: "tsqr_first_level", 1: "tsqr_upper_levels", 2: "svd_of_R", 3: "rank_and_core", 4: "tsmm",
+                 5: "input_range"}
 
 
 def tt_profile(enable: bool):
@@ -274,10 +278,17 @@ def tt_serve_create(budget_bytes, max_inflight=8, arena_bytes=0, timeout_s=60.0)
     return srv
 
 
-def tt_serve_submit(srv, job) -> int:
+def tt_serve_submit(srv, job, ready_stream=0) -> int:
+    """Queue a tt_job; its kernels wait for the work queued so far on ready_stream
+    (a cudaStream_t as int, 0 = the legacy default stream)."""
     t = C.c_uint64(0)
-    check(lib().tt_serve_submit(srv, C.byref(job), C.byref(t)), "tt_serve_submit")
+    check(lib().tt_serve_submit(srv, C.byref(job), ready_stream or None, C.byref(t)), "tt_serve_submit")
     return t.value
+
+
+def tt_serve_release(srv, ticket) -> int:
+    """Forget a finished request; TT_OK, TT_EAGAIN (still running) or TT_EINVAL."""
+    return lib().tt_serve_release(srv, ticket)
 
 
 def tt_serve_poll(srv, ticket, wait=False):
@@ -289,6 +300,25 @@ def tt_serve_poll(srv, ticket, wait=False):
 
 def tt_serve_destroy(srv):
     check(lib().tt_serve_destroy(srv), "tt_serve_destroy")
+
+
+TT_RANGE_NONE = -100000
+FMA_FP32, FMA_FP64, FMA_DF = 0, 1, 2
+
+
+def tt_fma_rate(kind, stream=0) -> float:
+    """Measured multiply-add rate of this GPU in flop/s (2 per multiply-add): FMA_FP32,
+    FMA_FP64 or FMA_DF (the lazy float-float multiply-add, FP64-equivalent)."""
+    v = C.c_double(0.0)
+    check(lib().tt_fma_rate(kind, C.byref(v), stream or None), "tt_fma_rate")
+    return v.value
+
+
+def tt_range_rule(sample_exp, seen_exp):
+    """(k_try, redo, k) of the FP64 form's exponent-range rule (see include/tt_svd.h)."""
+    a, b, c = C.c_int(0), C.c_int(0), C.c_int(0)
+    check(lib().tt_range_rule(sample_exp, seen_exp, C.byref(a), C.byref(b), C.byref(c)), "tt_range_rule")
+    return a.value, b.value, c.value
 
 
 def tt_tune_set(key: str, value: int):

@@ -13,6 +13,12 @@
 #include <stdint.h>
 #include <float.h>
 
+#include "engine.h"
+
+using tt::XRange;
+using tt::kXrBias;
+using tt::kXrNonfinite;
+
 struct __align__(8) df {
   float hi, lo;
 };
@@ -94,7 +100,7 @@ __device__ __forceinline__ df rcp_(df b) {
 }
 __device__ __forceinline__ df sqrt_(df a) {
   // one Newton correction of the FP32 root: x + (a - x^2) / (2x), residual in df
-  if (!(a.hi > 0.f)) return mkdf(0.f, 0.f);
+  if (!(a.hi > 0.f)) return a.hi != a.hi ? a : mkdf(0.f, 0.f);  // NaN stays NaN
   float x = sqrt_seed(a.hi);
   float p, e; eft_two_prod(x, x, p, e);
   df res = sub(a, mkdf(p, e));
@@ -102,6 +108,8 @@ __device__ __forceinline__ df sqrt_(df a) {
   return df_norm(x, corr);
 }
 __device__ __forceinline__ bool is_pos(df a) { return a.hi > 0.f; }
+__device__ __forceinline__ float fp32_lead(df a) { return a.hi; }
+__device__ __forceinline__ float fp32_lead(float a) { return a; }
 __device__ __forceinline__ bool is_gt(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 __device__ __forceinline__ df abs_(df a) { return a.hi < 0.f ? neg(a) : a; }
 __device__ __forceinline__ double to_f64(df a) { return (double)a.hi + (double)a.lo; }
@@ -122,7 +130,7 @@ __device__ __forceinline__ double fmac(double a, double b, double c) { return __
 __device__ __forceinline__ double fnmac(double a, double b, double c) { return __fma_rn(-a, b, c); }
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 __device__ __forceinline__ double rcp_(double b) { return 1.0 / b; }
-__device__ __forceinline__ double sqrt_(double a) { return a > 0.0 ? sqrt(a) : 0.0; }
+__device__ __forceinline__ double sqrt_(double a) { return a > 0.0 ? sqrt(a) : (a != a ? a : 0.0); }
 __device__ __forceinline__ bool is_pos(double a) { return a > 0.0; }
 __device__ __forceinline__ bool is_gt(double a, double b) { return a > b; }
 __device__ __forceinline__ double abs_(double a) { return fabs(a); }
@@ -138,7 +146,7 @@ __device__ __forceinline__ float fmac(float a, float b, float c) { return __fmaf
 __device__ __forceinline__ float fnmac(float a, float b, float c) { return __fmaf_rn(-a, b, c); }
 __device__ __forceinline__ float div_(float a, float b) { return a / b; }
 __device__ __forceinline__ float rcp_(float b) { return 1.0f / b; }
-__device__ __forceinline__ float sqrt_(float a) { return a > 0.f ? sqrtf(a) : 0.f; }
+__device__ __forceinline__ float sqrt_(float a) { return a > 0.f ? sqrtf(a) : (a != a ? a : 0.f); }
 __device__ __forceinline__ bool is_pos(float a) { return a > 0.f; }
 __device__ __forceinline__ bool is_gt(float a, float b) { return a > b; }
 __device__ __forceinline__ float abs_(float a) { return fabsf(a); }
@@ -253,28 +261,114 @@ template <> struct Tr<df> {
   }
 };
 
-// df from an FP64 value without FP64 instructions: hi = the FP64 value cut to
-// 24 significant bits, lo = the next 23 bits (47 bits kept).  Exponents outside
-// the normal FP32 range flush to zero / overflow to infinity.
-__device__ __forceinline__ df df_from_f64_bits(double x) {
+// ----------------------------------------------------------------------------
+// The Householder reflector of one column (Alg. 6): panel part y with D = ||y||^2 and
+// pivot entry R_jj.  alpha = -sign(R_jj) sqrt(R_jj^2 + D) becomes the new R_jj; with
+// v = [R_jj - alpha; y] and t = ||v||^2 / 2 the reflector is I - v v^T / t.  Returns
+// alpha, piv = R_jj - alpha and rt = 1 / t.
+template <class C>
+struct Refl {
+  C alpha, piv, rt;
+};
+// Native FP64: the guard eps_FP of Alg. 6 (DBL_MIN) keeps t > 0 for a zero column.
+__device__ __forceinline__ Refl<double> householder(double rjj, double D, double eps) {
+  double t = fmac(rjj, rjj, D) + eps;
+  double alpha = sqrt_(t + eps);
+  if (rjj > 0.0) alpha = -alpha;
+  t = fnmac(alpha, rjj, t);
+  return {alpha, rjj - alpha, 1.0 / t};
+}
+// FP32 and float-float read their input shifted so that max |x| lies in [0.5, 1)
+// (engine.h, XRange).  There an additive FLT_MIN would be a relative error of t for any
+// column of norm below ~2^-39, and the reflector would no longer be orthogonal.  Instead a
+// column with R_jj^2 + D < 2^-100 (norm below 2^-50 of the largest input entry) is left
+// as it is: the reflector is the identity (rt = 0, alpha = R_jj), which drops at most
+// 2^-50 max|x| of that column's remainder.
+constexpr float kReflTiny = 7.8886090522101181e-31f;  // 2^-100
+template <class C>
+__device__ __forceinline__ Refl<C> householder_shifted(C rjj, C D) {
+  C t = fmac(rjj, rjj, D);
+  if (fp32_lead(t) < kReflTiny) return {rjj, Tr<C>::zero(), Tr<C>::zero()};
+  C alpha = sqrt_(t);
+  if (is_pos(rjj)) alpha = neg(alpha);
+  t = fnmac(alpha, rjj, t);
+  return {alpha, sub(rjj, alpha), rcp_(t)};
+}
+__device__ __forceinline__ Refl<float> householder(float rjj, float D, float) {
+  return householder_shifted<float>(rjj, D);
+}
+__device__ __forceinline__ Refl<df> householder(df rjj, df D, df) {
+  return householder_shifted<df>(rjj, D);
+}
+
+// A value of a matrix already scaled to max |a| in [0.5, 1), with entries below 2^-62 set
+// to zero in float-float: their squares would leave FP32's normal range (the Jacobi
+// sweeps compare products of column norms); they change no singular value by more than
+// 2^-62 m of the largest entry.  FP64 and FP32 values are returned unchanged.
+__device__ __forceinline__ df flush_tiny(df a) {
+  return fabsf(a.hi) < 2.168404344971009e-19f ? mkdf(0.f, 0.f) : a;  // 2^-62
+}
+__device__ __forceinline__ double flush_tiny(double a) { return a; }
+__device__ __forceinline__ float flush_tiny(float a) { return a; }
+
+// df from an FP64 value times 2^-sh without FP64 instructions: hi = the scaled value cut
+// to 24 significant bits, lo = the next 23 bits (47 bits kept).  A subnormal input is
+// first scaled up exactly by 2^64 (one FP64 multiply, only on that rare path).  Scaled
+// exponents below the normal FP32 range flush to zero, above it overflow to infinity;
+// the caller picks sh so that neither happens to entries that matter (engine.h, XRange).
+__device__ __forceinline__ df df_from_f64_sh(double x, int sh) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  int e = (int)((b >> 52) & 0x7FF);
+  unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  if (e == 0) {
+    if (mant == 0ull) return mkdf(0.f, 0.f);
+    // subnormal: move the leading bit to the implicit position (integer operations only);
+    // the exponent field becomes 1 - s <= 0
+    const int s = __clzll((long long)mant) - 11;
+    mant = (mant << s) & 0xFFFFFFFFFFFFFull;
+    e = 1 - s;
+  }
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7FF);
-  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-  const int fe = e - 1023 + 127;
+  if (e == 2047)  // infinity stays infinity, NaN stays NaN
+    return mkdf(__int_as_float((int)(sign | 0x7F800000u | (mant ? 0x400000u : 0u))), 0.f);
+  const int fe = e - 1023 + 127 - sh;
   if (fe <= 0) return mkdf(0.f, 0.f);
   if (fe >= 255) return mkdf(__int_as_float((int)(sign | 0x7F800000u)), 0.f);
   const float hi = __int_as_float((int)(sign | ((unsigned)fe << 23) | (unsigned)(mant >> 29)));
   // remaining 29 bits; keep the top 23 of them as an exact small integer
   const unsigned rem23 = (unsigned)((mant & 0x1FFFFFFFull) >> 6);
   const float f = __fsub_rn(__int_as_float((int)(0x4B000000u | rem23)), 8388608.0f);
-  // value of one unit of rem23: 2^(e - 1023 - 52 + 6)
-  const int se = e - 1069 + 127;
+  // value of one unit of rem23: 2^(e - 1023 - 52 + 6 - sh)
+  const int se = e - 1069 + 127 - sh;
   const float scale = se > 0 ? __int_as_float(se << 23) : 0.f;
   float lo = __fmul_rn(f, scale);
   lo = sign ? -lo : lo;
   return mkdf(hi, lo);
 }
+__device__ __forceinline__ df df_from_f64_bits(double x) { return df_from_f64_sh(x, 0); }
+
+// encoded exponent (engine.h, XRange) of an FP32 value, subnormals included: 0 for zero
+__device__ __forceinline__ int f32_expo_enc(float x) {
+  const unsigned b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xFF);
+  if (e == 255) return kXrNonfinite;
+  if (e != 0) return e - 127 + kXrBias;
+  if ((b << 1) == 0u) return 0;
+  return (int)((__float_as_uint(x * 16777216.0f) >> 23) & 0xFF) - 127 - 24 + kXrBias;
+}
+__device__ __forceinline__ int expo_enc(float x) { return f32_expo_enc(x); }
+
+// encoded exponent (engine.h, XRange) of an FP64 value, subnormals included: 0 for zero
+__device__ __forceinline__ int f64_expo_enc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 2047) return kXrNonfinite;
+  if (e != 0) return e - 1023 + kXrBias;
+  if ((b << 1) == 0ull) return 0;
+  return (int)((__double_as_longlong(x * 18446744073709551616.0) >> 52) & 0x7FF) - 1023 - 64 +
+         kXrBias;
+}
+__device__ __forceinline__ int expo_enc(double x) { return f64_expo_enc(x); }
 
 // storage -> compute
 template <class C, class S> struct Ld;
@@ -300,3 +394,112 @@ template <> struct St<double, float> { __device__ static double f(float x) { ret
 template <> struct St<df, float> { __device__ static df f(float x) { return mkdf(x, 0.f); } };
 template <> struct St<df, double> { __device__ static df f(double x) { return Tr<df>::of(x); } };
 template <class S, class C> __device__ __forceinline__ S st_as(C x) { return St<S, C>::f(x); }
+
+// Entries below 2^-62 of 2^sh (the largest magnitude is in [2^(sh-1), 2^sh)) are read as
+// zero: their squares and products would leave FP32's normal range, where a Householder
+// reflector built from underflowed sums is no longer orthogonal.  Over n entries this
+// changes X by at most sqrt(n) 2^-62 max|x| in the Frobenius norm (2^-47 max|x| for 2^30
+// entries), below the float-float rounding of the decomposition.
+constexpr int kXrFlush = 62;
+
+// Reader of the input X of a level: the plain storage-to-compute conversion, except FP64
+// read in float-float and FP32 read in FP32 or float-float, which are shifted by 2^-sh
+// and record the largest exponent they met (two integer instructions per entry).
+template <class C, class S>
+struct XRead {
+  int sh = 0;
+  bool flush = false;
+  unsigned efield = 0;
+  __device__ __forceinline__ C operator()(S x) { return Ld<C, S>::f(x); }
+  __device__ __forceinline__ static int seen_of(unsigned) { return 0; }
+};
+template <>
+struct XRead<df, double> {
+  int sh = 0;
+  bool flush = false;    // true once sh comes from the input's exponent range
+  unsigned efield = 0;   // largest (hi word & 0x7FF00000) seen, i.e. the exponent field << 20
+  __device__ __forceinline__ df operator()(double x) {
+    const unsigned h = (unsigned)__double2hiint(x) & 0x7FF00000u;
+    efield = max(efield, h);
+    if (!flush) return df_from_f64_sh(x, sh);
+    // floor(log2 |x|) < sh - kXrFlush: for a normal x its exponent field is below
+    // 1023 + sh - kXrFlush; a subnormal x (field 0, |x| < 2^-1022) is below whenever
+    // sh - kXrFlush > -1023 (otherwise the whole tensor is of subnormal size: kept)
+    const int f = (int)(h >> 20);
+    if (f != 0 ? f < 1023 + sh - kXrFlush : sh - kXrFlush > -1023) return mkdf(0.f, 0.f);
+    return df_from_f64_sh(x, sh);
+  }
+  // encoded exponent (engine.h, XRange) of the largest field (subnormals count as zero:
+  // only large entries can leave the safe window)
+  __device__ __forceinline__ static int seen_of(unsigned ef) {
+    const int f = (int)(ef >> 20);
+    return f == 0 ? 0 : (f == 2047 ? kXrNonfinite : f - 1023 + kXrBias);
+  }
+};
+// FP32 value times 2^-sh, exactly (exponent arithmetic); with `flush`, values below
+// 2^(sh - kXrFlush) are read as zero (the same rule as for FP64 input)
+__device__ __forceinline__ float f32_shift(float x, int sh, bool flush) {
+  unsigned b = __float_as_uint(x);
+  int e = (int)((b >> 23) & 0xFF);
+  if (e == 255) return x;                 // infinity, NaN
+  if (e == 0) {
+    if ((b << 1) == 0u) return x;         // +-0
+    b = __float_as_uint(x * 16777216.0f); // subnormal: x 2^24, exact
+    e = (int)((b >> 23) & 0xFF);
+    sh += 24;
+  }
+  if (flush && e - 127 < sh - kXrFlush) return 0.f;
+  const int fe = e - sh;
+  if (fe <= 0) return 0.f;
+  if (fe >= 255) return __uint_as_float((b & 0x80000000u) | 0x7F800000u);
+  return __uint_as_float((b & 0x807FFFFFu) | ((unsigned)fe << 23));
+}
+template <>
+struct XRead<float, float> {
+  int sh = 0;
+  bool flush = false;
+  unsigned efield = 0;   // largest (bits & 0x7F800000) seen, i.e. the exponent field << 23
+  __device__ __forceinline__ float operator()(float x) {
+    efield = max(efield, __float_as_uint(x) & 0x7F800000u);
+    return f32_shift(x, sh, flush);
+  }
+  // encoded exponent (engine.h, XRange) of the largest field (subnormals count as zero)
+  __device__ __forceinline__ static int seen_of(unsigned ef) {
+    const int f = (int)(ef >> 23);
+    return f == 0 ? 0 : (f == 255 ? kXrNonfinite : f - 127 + kXrBias);
+  }
+};
+template <>
+struct XRead<df, float> {
+  XRead<float, float> r;
+  int sh = 0;
+  bool flush = false;
+  unsigned efield = 0;
+  __device__ __forceinline__ df operator()(float x) {
+    r.sh = sh;
+    r.flush = flush;
+    const float v = r(x);
+    efield = r.efield;
+    return mkdf(v, 0.f);
+  }
+  __device__ __forceinline__ static int seen_of(unsigned ef) { return XRead<float, float>::seen_of(ef); }
+};
+// Start of a level kernel that reads X through `rd`: false when this launch is the
+// re-run of the first level and the first pass was fine (the kernel then returns).
+template <class C, class S>
+__device__ __forceinline__ bool xr_begin(const XRange* xr, int xfix, XRead<C, S>& rd) {
+  if (!xr) return true;
+  if (xfix && !xr->redo) return false;
+  rd.sh = xfix ? xr->k : tt::xr_shift_for(xr->sample);
+  rd.flush = true;
+  return true;
+}
+// End of such a kernel: the largest exponent of the first pass, one atomic per warp.
+template <class C, class S>
+__device__ __forceinline__ void xr_end(XRange* xr, int xfix, const XRead<C, S>& rd) {
+  if (!xr || xfix) return;
+  unsigned e = rd.efield;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0 && e) atomicMax(&xr->seen, XRead<C, S>::seen_of(e));
+}

@@ -635,6 +635,26 @@ struct HostIn {
   std::vector<cudaEvent_t> ev;
 };
 
+// largest encoded exponent (engine.h, XRange) of a strided sample of a host array
+template <class T>
+static int host_sample_enc(const T* X, int64_t count) {
+  const int64_t ns = std::min<int64_t>(count, 4096);
+  const int64_t stride = ns > 0 ? count / ns : 1;
+  int best = 0;
+  for (int64_t j = 0; j < ns; ++j) {
+    const double x = (double)X[j * stride];
+    int e = 0;
+    if (!std::isfinite(x)) e = kXrNonfinite;
+    else if (x != 0.0) {
+      int ex = 0;
+      std::frexp(x, &ex);  // |x| = f 2^ex with f in [0.5, 1)
+      e = ex - 1 + kXrBias;
+    }
+    best = std::max(best, e);
+  }
+  return best;
+}
+
 static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out,
                           int64_t* ranks_out, double* sigma_out, double* err2_out, void* work,
                           cudaStream_t s, HostIn* hin = nullptr) {
@@ -645,6 +665,22 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
   int64_t sig_stride = 0, sig_count = 0;
   sigma_layout(d, P.n, P.r_worst, &sig_stride, &sig_count);
   TT_CK(launch_init_state(st, d, P.n, s));
+  // FP64 input in float-float and FP32 input: the exponent shift of X (engine.h, XRange)
+  XRange* xr = (P.comp_tsqr1 == Fmt::DF || P.xfmt == Fmt::F32) ? &st->xr : nullptr;
+  bool first_active = true;
+  if (xr) {
+    int64_t nbar = 1;
+    for (int a = 0; a < d; ++a) nbar *= P.n[a];
+    if (hin && hin->X_host) {
+      const void* xh = hin->X_host;
+      const int enc = P.xfmt == Fmt::F32 ? host_sample_enc(static_cast<const float*>(xh), nbar)
+                                         : host_sample_enc(static_cast<const double*>(xh), nbar);
+      TT_CK(launch_range_set_sample(xr, enc, s));
+    } else {
+      TT_CK(launch_range_sample(P.xfmt, X, nbar, xr, s));
+    }
+    ++g_launches;
+  }
   if (hin && hin->X_host) {
     // X is copied in row blocks by the first TSQR level when that level reads it;
     // otherwise (every step elided) in one piece here
@@ -694,39 +730,57 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
       int64_t ldRfin = 0;
       Fmt rfmt = Fmt::DF;
       for (size_t l = 0; l < S.levels.size(); ++l) {
-        const TsqrLevel& L = S.levels[l];
+        TsqrLevel L = S.levels[l];
         void* Rout = wb + P.off_R[l & 1];
         const int64_t ldR = L.warps * L.mb;
-        if (L.chunks > 1) {
-          // first level in row blocks: block c (rows r0..r1 of every column) is copied from the
-          // host when X comes from there, and its launch waits only for that copy
-          prof::Scope ps(0, i, (double)L.rows * mm * fmt_bytes(L.in), 2.0 * (double)L.rows * mm * mm, s);
-          const size_t es = fmt_bytes(L.in);
-          for (int c = 0; c < L.chunks; ++c) {
-            const int64_t r0 = (int64_t)c * L.chunk_rows;
-            const int64_t r1 = std::min<int64_t>(L.rows, r0 + L.chunk_rows);
-            if (hin && hin->X_host && lin == X) {
-              TT_CK(cudaMemcpy2DAsync(static_cast<char*>(const_cast<void*>(X)) + r0 * es, lld * es,
-                                      hin->X_host + r0 * es, lld * es, (size_t)(r1 - r0) * es,
-                                      (size_t)S.m_max, cudaMemcpyHostToDevice, hin->cs));
-              TT_CK(cudaEventRecord(hin->ev[c], hin->cs));
-              TT_CK(cudaStreamWaitEvent(s, hin->ev[c], 0));
+        // one launch of level L, or of each of its row blocks (xfix: the re-run pass)
+        auto launch_level = [&](int xfix) -> tt_status {
+          L.xfix = xfix;
+          if (L.chunks > 1) {
+            // first level in row blocks: block c (rows r0..r1 of every column) is copied from
+            // the host when X comes from there, and its launch waits only for that copy
+            const size_t es = fmt_bytes(L.in);
+            for (int c = 0; c < L.chunks; ++c) {
+              const int64_t r0 = (int64_t)c * L.chunk_rows;
+              const int64_t r1 = std::min<int64_t>(L.rows, r0 + L.chunk_rows);
+              if (!xfix && hin && hin->X_host && lin == X) {
+                TT_CK(cudaMemcpy2DAsync(static_cast<char*>(const_cast<void*>(X)) + r0 * es, lld * es,
+                                        hin->X_host + r0 * es, lld * es, (size_t)(r1 - r0) * es,
+                                        (size_t)S.m_max, cudaMemcpyHostToDevice, hin->cs));
+                TT_CK(cudaEventRecord(hin->ev[c], hin->cs));
+                TT_CK(cudaStreamWaitEvent(s, hin->ev[c], 0));
+              }
+              TsqrLevel Lc = L;
+              Lc.rows = r1 - r0;
+              Lc.panels = (Lc.rows + L.pr - 1) / L.pr;
+              Lc.chunks = 1;
+              Lc.warps = L.chunk_parts;
+              char* Rc = static_cast<char*>(Rout) + (size_t)c * L.chunk_parts * L.mb * fmt_bytes(L.out);
+              TT_CK(launch_tsqr_level(Lc, static_cast<const char*>(lin) + r0 * es, lld, &st->m[i], Rc,
+                                      ldR, wb + P.off_Rscr, status, s));
+              ++g_launches;
             }
-            TsqrLevel Lc = L;
-            Lc.rows = r1 - r0;
-            Lc.panels = (Lc.rows + L.pr - 1) / L.pr;
-            Lc.chunks = 1;
-            Lc.warps = L.chunk_parts;
-            char* Rc = static_cast<char*>(Rout) + (size_t)c * L.chunk_parts * L.mb * fmt_bytes(L.out);
-            TT_CK(launch_tsqr_level(Lc, static_cast<const char*>(lin) + r0 * es, lld, &st->m[i], Rc,
-                                    ldR, wb + P.off_Rscr, status, s));
-            ++g_launches;
+            return TT_OK;
           }
-        } else {
-          prof::Scope ps(l == 0 ? 0 : 1, i, (double)L.rows * mm * fmt_bytes(L.in),
-                         2.0 * (double)L.rows * mm * mm, s);
           TT_CK(launch_tsqr_level(L, lin, lld, &st->m[i], Rout, ldR, wb + P.off_Rscr, status, s));
           ++g_launches;
+          return TT_OK;
+        };
+        {
+          prof::Scope ps(l == 0 ? 0 : 1, i, (double)L.rows * mm * fmt_bytes(L.in),
+                         2.0 * (double)L.rows * mm * mm, s);
+          if (xr && first_active && l == 0) L.xr = xr;  // this level reads X
+          const tt_status e = launch_level(0);
+          if (e != TT_OK) return e;
+        }
+        if (L.xr) {
+          // keep the shift, or run the level again with the shift of the largest entry it met
+          // (that launch returns at once when the shift was kept)
+          prof::Scope ps(5, i, 0.0, 0.0, s);
+          TT_CK(launch_range_decide(xr, s));
+          ++g_launches;
+          const tt_status e = launch_level(1);
+          if (e != TT_OK) return e;
         }
         lin = Rout;
         lld = ldR;
@@ -755,17 +809,21 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
       const double rr = (double)S.r_max_out;
       prof::Scope ps(4, i, (double)rows * (mm * fmt_bytes(S.in_fmt) + rr * fmt_bytes(P.inter)),
                      2.0 * (double)rows * mm * rr, s);
-      TT_CK(launch_tsmm(S.tsmm, cur, rows, rows, &st->m[i], Vout, P.ldA, &st->r[i - 1], Y, rows,
+      TsmmCfg tc = S.tsmm;
+      if (xr && first_active) tc.xr = xr;
+      TT_CK(launch_tsmm(tc, cur, rows, rows, &st->m[i], Vout, P.ldA, &st->r[i - 1], Y, rows,
                         status, s));
       ++g_launches;
     }
+    first_active = false;
     cur = Y;
     cur_fmt = P.inter;
     rows /= P.n[i - 2];
   }
   // T^(1) = W^(1): n_1 x r_1 (worst case converted; only r_0 n_1 r_1 entries are meaningful)
   const int64_t cnt = P.n[0] * (int64_t)P.r_worst[1];
-  TT_CK(launch_convert_to_f64(cur_fmt, cur, cnt, cores_out[0], s));
+  // a W that went through the shifted pipeline carries the factor 2^-k; X itself does not
+  TT_CK(launch_convert_to_f64(cur_fmt, cur, cnt, cores_out[0], s, cur == X ? nullptr : xr));
   TT_CK(launch_finish(st, d, ranks_out, err2_out, s));
   g_launches += 2;
   return TT_OK;
@@ -783,6 +841,15 @@ static tt_status run_two_sided(const TsPlan& T, const void* X, double* const* co
   TT_CK(launch_init_state(st, T.d, T.n, s));
   TT_CK(launch_zero(e, s));
   g_launches += 2;
+  // FP64 input in float-float and FP32 input: the exponent shift of X (engine.h, XRange)
+  XRange* xr = (T.comp_tsqr1 == Fmt::DF || T.xfmt == Fmt::F32) ? &st->xr : nullptr;
+  if (xr) {
+    int64_t nbar = 1;
+    for (int a = 0; a < T.d; ++a) nbar *= T.n[a];
+    TT_CK(launch_range_sample(T.xfmt, X, nbar, xr, s));
+    ++g_launches;
+  }
+  bool first_active = true;
   auto zptr = [&](int z) -> const void* { return z < 0 ? X : (const void*)(wb + T.off_Z[z]); };
   for (const TsStep& S : T.steps) {
     double* core = cores_out[S.dim - 1];
@@ -805,14 +872,23 @@ static tt_status run_two_sided(const TsPlan& T, const void* X, double* const* co
     int64_t ldRfin = 0;
     Fmt rfmt = Fmt::DF;
     for (size_t l = 0; l < S.levels.size(); ++l) {
-      const TsqrLevel& L = S.levels[l];
+      TsqrLevel L = S.levels[l];
       void* Rout = wb + T.off_R[l & 1];
       const int64_t ldR = L.warps * L.mb;
       {
         prof::Scope ps(l == 0 ? 0 : 1, S.dim, (double)L.rows * S.m * fmt_bytes(L.in),
                        2.0 * (double)L.rows * S.m * S.m, s);
+        if (xr && first_active && l == 0) L.xr = xr;  // this level reads X (or its transpose)
         TT_CK(launch_tsqr_level(L, lin, lld, nullptr, Rout, ldR, wb + T.off_Rscr, status, s));
         ++g_launches;
+      }
+      if (L.xr) {
+        // keep the shift, or run the level again with the shift of the largest entry it met
+        prof::Scope ps(5, S.dim, 0.0, 0.0, s);
+        TT_CK(launch_range_decide(xr, s));
+        L.xfix = 1;
+        TT_CK(launch_tsqr_level(L, lin, lld, nullptr, Rout, ldR, wb + T.off_Rscr, status, s));
+        g_launches += 2;
       }
       lin = Rout;
       lld = ldR;
@@ -834,9 +910,12 @@ static tt_status run_two_sided(const TsPlan& T, const void* X, double* const* co
     {
       prof::Scope ps(4, S.dim, (double)S.rows * (S.m * fmt_bytes(S.in) + S.r * fmt_bytes(T.inter)),
                      2.0 * (double)S.rows * S.m * S.r, s);
-      TT_CK(launch_tsmm(S.tsmm, W, S.rows, S.rows, nullptr, Vout, T.ldA, nullptr, Y, S.rows, status, s));
+      TsmmCfg tc = S.tsmm;
+      if (xr && first_active) tc.xr = xr;
+      TT_CK(launch_tsmm(tc, W, S.rows, S.rows, nullptr, Vout, T.ldA, nullptr, Y, S.rows, status, s));
       ++g_launches;
     }
+    first_active = false;
     if (!S.right) {
       // back to the (r, n_{a+1}, ..., r_R) layout of Z
       TT_CK(launch_transpose(fmt_bytes(T.inter), Y, S.rows, S.r, Zout, s));
@@ -844,8 +923,10 @@ static tt_status run_two_sided(const TsPlan& T, const void* X, double* const* co
     }
   }
   const int64_t cnt = (int64_t)T.rl * T.n[T.mid - 1] * T.rr;
-  TT_CK(launch_convert_to_f64(T.zfmt_final, zptr(T.zfinal), cnt, cores_out[T.mid - 1], s));
-  TT_CK(launch_put_ranks(T.ranks, T.d + 1, ranks_out, e, err2_out, s));
+  // the middle core carries the factor 2^-k of the shifted pipeline unless it is X itself
+  TT_CK(launch_convert_to_f64(T.zfmt_final, zptr(T.zfinal), cnt, cores_out[T.mid - 1], s,
+                              T.zfinal < 0 ? nullptr : xr));
+  TT_CK(launch_put_ranks(T.ranks, T.d + 1, ranks_out, e, err2_out, s, xr));
   g_launches += 2;
   return TT_OK;
 }
@@ -900,6 +981,18 @@ const char* tt_status_str(tt_status s) {
 }
 
 const char* tt_last_error(void) { return g_last_err; }
+
+tt_status tt_range_rule(int sample_exp, int seen_exp, int* k_try, int* redo, int* k) {
+  if (!k_try || !redo || !k) return TT_EINVAL;
+  auto enc = [](int e) { return e == TT_RANGE_NONE ? 0 : e + kXrBias; };
+  if ((sample_exp != TT_RANGE_NONE && (sample_exp < -1200 || sample_exp > 1100)) ||
+      (seen_exp != TT_RANGE_NONE && (seen_exp < -1200 || seen_exp > 1100)))
+    return TT_EINVAL;
+  *k_try = xr_shift_for(enc(sample_exp));
+  *redo = xr_needs_redo(*k_try, enc(seen_exp)) ? 1 : 0;
+  *k = *redo ? xr_shift_for(enc(seen_exp)) : *k_try;
+  return TT_OK;
+}
 
 tt_status tt_tune_set(const char* key, int value) {
   if (!key || !*key) return TT_EINVAL;
@@ -1171,8 +1264,12 @@ tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, d
   size_t szR = 0;
   for (auto& L : lv) szR = std::max(szR, (size_t)L.warps * L.mb * m * fmt_bytes(L.out));
   char* wb = static_cast<char*>(work);
+  // the first 256 bytes: the status word, then the exponent range of W (FP64 input)
   int* status = reinterpret_cast<int*>(wb);
-  TT_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+  XRange* xr = reinterpret_cast<XRange*>(wb + 16);
+  TT_CK(cudaMemsetAsync(wb, 0, 256, s));
+  // (a strided W: the first pass starts unshifted and is redone if that was wrong)
+  if (ld == rows) TT_CK(launch_range_sample(in, W, rows * (int64_t)m, xr, s));
   char* R0 = wb + align256(256);
   char* R1 = R0 + align256(szR);
   char* scr = R1 + align256(szR);
@@ -1184,14 +1281,22 @@ tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, d
   for (size_t l = 0; l < lv.size(); ++l) {
     void* Rout = (l & 1) ? R1 : R0;
     const int64_t ldR = lv[l].warps * lv[l].mb;
-    TT_CK(launch_tsqr_level(lv[l], lin, lld, nullptr, Rout, ldR, scr, status, s));
+    TsqrLevel L = lv[l];
+    if (l == 0) L.xr = xr;
+    TT_CK(launch_tsqr_level(L, lin, lld, nullptr, Rout, ldR, scr, status, s));
+    if (L.xr) {
+      TT_CK(launch_range_decide(xr, s));
+      L.xfix = 1;
+      TT_CK(launch_tsqr_level(L, lin, lld, nullptr, Rout, ldR, scr, status, s));
+    }
     lin = Rout;
     lld = ldR;
     Rfin = Rout;
     ldRfin = ldR;
     rf = lv[l].out;
   }
-  return cuda_err(launch_copy_mat_f64(rf, Rfin, ldRfin, m, m, 1, R_out, m, s));
+  // R of W = 2^k times the R of the shifted W
+  return cuda_err(launch_copy_mat_f64(rf, Rfin, ldRfin, m, m, 1, R_out, m, s, xr));
 }
 
 tt_status tt_small_svd_query(int m, size_t* work_bytes) {

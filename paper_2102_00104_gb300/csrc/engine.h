@@ -22,9 +22,44 @@ enum : int {
 // wait limit of in-kernel spin-waits, in SM clock cycles (~2 s at 2 GHz)
 constexpr long long kWaitCycles = 4000000000LL;
 
+// Exponent range of an FP64 input read in float-float.  Float-float has FP32's
+// exponent range, so X is read as X * 2^-k with an exact power of two k chosen from its
+// largest magnitude; sigma, the discarded energy and the last core are scaled back.
+// A strided sample of X gives k_try; the first TSQR level reads with k_try and records
+// the largest exponent it meets; when that lies far above the sample, the level is run
+// again with the shift of the true largest magnitude (redo = 1).  Every later reader of
+// X uses k.  Exponents are stored encoded so that all-zero bytes mean "none seen":
+// enc = e + kXrBias for a finite nonzero value 2^e <= |x| < 2^(e+1), kXrNonfinite for
+// infinity and NaN.
+struct XRange {
+  int sample;  // largest encoded exponent of the strided sample
+  int seen;    // largest encoded exponent met by the first pass of the first TSQR level
+  int redo;    // 1: the first level runs again with k
+  int k;       // the shift of every other reader of X, and of the results
+};
+constexpr int kXrBias = 2048;
+constexpr int kXrNonfinite = 8192;
+constexpr int kXrWindow = 40;      // entries up to 2^40 after the shift keep every sum of
+                                   // squares inside FP32's range for up to 2^46 rows
+// shift that brings the largest magnitude (encoded exponent) into [0.5, 1); 0 when
+// nothing nonzero and finite was seen
+__host__ __device__ inline int xr_shift_for(int enc) {
+  return (enc <= 0 || enc >= kXrNonfinite) ? 0 : enc - kXrBias + 1;
+}
+// the first pass read with k_try; true when its largest entry left the safe window
+// (above it: sums of squares could overflow; below it: they could underflow -- the
+// latter only when no sample was taken)
+__host__ __device__ inline bool xr_needs_redo(int k_try, int seen) {
+  if (seen <= 0 || seen >= kXrNonfinite) return false;
+  const int top = seen - kXrBias - k_try;
+  return top > kXrWindow || top < -kXrWindow;
+}
+
 // per-call device state (lives in the workspace)
 struct DevState {
   int status;
+  int pad_;
+  XRange xr;
   int first_done;              // 1 once delta has been fixed (Alg. 2 line 7)
   double delta2;
   double err2;
@@ -62,6 +97,8 @@ struct TsqrLevel {
   int64_t panels;
   size_t smem;       // dynamic smem per CTA
   Fmt in, comp, out;
+  XRange* xr = nullptr;       // first level of FP64 input in float-float: exponent shift
+  int xfix = 0;               // 1: the re-run of that level (returns at once unless xr->redo)
   int chunks = 1;            // first level only: launched once per row block of chunk_rows
   int64_t chunk_rows = 0;    // rows with the full grid; each block writes chunk_parts partial
   int64_t chunk_parts = 0;   // R's, so warps = chunks * chunk_parts
@@ -130,7 +167,8 @@ cudaError_t launch_core_identity(int m, double* core, cudaStream_t s);
 cudaError_t launch_set_rank(DevState* st, int step_i, int n_next, int r, cudaStream_t s);
 // dst(i, k) = src(i, k) as FP64 for i < rows, k < cols (zero below the diagonal if upper)
 cudaError_t launch_copy_mat_f64(Fmt f, const void* src, int64_t lds, int rows, int cols, int upper,
-                                double* dst, int64_t ldd, cudaStream_t s);
+                                double* dst, int64_t ldd, cudaStream_t s,
+                                const XRange* xr = nullptr);
 cudaError_t launch_merge_core(const double* Told, const double* S0, int ab, int r, int rho,
                               double* Tnew, cudaStream_t s);
 cudaError_t launch_join_ranks(const int64_t* r1, int p, const int64_t* r2, int q, int64_t* out,
@@ -143,10 +181,18 @@ cudaError_t launch_core_side(Fmt vfmt, bool left, const void* V, int ldV, int m,
                              cudaStream_t s);
 cudaError_t launch_add_discarded(const double* sigma, int cnt, int r, double* e, cudaStream_t s);
 cudaError_t launch_zero(double* e, cudaStream_t s);
+// err2_out = e[0] * 2^(2 xr->k) (xr may be null)
 cudaError_t launch_put_ranks(const int64_t* ranks, int count, int64_t* ranks_out, const double* e,
-                             double* err2_out, cudaStream_t s);
+                             double* err2_out, cudaStream_t s, const XRange* xr = nullptr);
+// dst = src * 2^xr->k (xr may be null: no scaling)
 cudaError_t launch_convert_to_f64(Fmt f, const void* src, int64_t count, double* dst,
-                                  cudaStream_t s);
+                                  cudaStream_t s, const XRange* xr = nullptr);
+// the exponent range of X from a strided sample (sets k_try = k, seen, redo), and the
+// decision after the first pass of the first TSQR level
+cudaError_t launch_range_sample(Fmt f, const void* X, int64_t count, XRange* xr, cudaStream_t s);
+cudaError_t launch_range_decide(XRange* xr, cudaStream_t s);
+// xr->sample = enc (a sample taken on the host, for input that is still in host memory)
+cudaError_t launch_range_set_sample(XRange* xr, int enc, cudaStream_t s);
 cudaError_t launch_fill_nan(double* dst, int64_t count, cudaStream_t s);
 cudaError_t launch_init_state(DevState* st, int d, const int64_t* n_host, cudaStream_t s);
 cudaError_t launch_finish(const DevState* st, int d, int64_t* ranks_out, double* err2_out,
@@ -167,6 +213,7 @@ struct TsmmCfg {
   int mstr;         // smem row stride (elements)
   size_t smem;
   int64_t ctas;
+  const XRange* xr = nullptr;  // FP64 input in float-float: W is read as W * 2^-xr->k
 };
 TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int64_t rows,
                   int num_sms);

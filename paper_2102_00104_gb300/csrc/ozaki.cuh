@@ -58,10 +58,11 @@ __device__ __forceinline__ unsigned oz_key(df x) { return (unsigned)__float_as_i
 __device__ __forceinline__ unsigned oz_key(double x) {
   return (unsigned)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7FF00000u;
 }
-__device__ __forceinline__ int oz_bexp_of(unsigned key, df*) { return (int)(key >> 23); }
-__device__ __forceinline__ int oz_bexp_of(unsigned key, double*) {
+__device__ __forceinline__ int oz_bexp_of(unsigned key, df*, int = 0) { return (int)(key >> 23); }
+// FP64 values read as x 2^-sh (the input's exponent shift, engine.h XRange)
+__device__ __forceinline__ int oz_bexp_of(unsigned key, double*, int sh = 0) {
   const int e = (int)(key >> 20);
-  const int f = e - 896;
+  const int f = e - 896 - sh;
   return e == 0 ? 0 : (f < 1 ? 1 : (f > 254 ? 254 : f));
 }
 // 2^-E with E = be - 126, for scaling values into (-1, 1)

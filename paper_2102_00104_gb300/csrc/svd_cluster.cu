@@ -127,7 +127,7 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
     if (tid == 0) colid[k] = col;
     for (int i = tid; i < m; i += nt) {
       C a = Tr<C>::zero();
-      if (col < m && i <= col) a = pow2s<C>(ld_as<C>(R[i + (int64_t)col * ldR]), -ex);
+      if (col < m && i <= col) a = flush_tiny(pow2s<C>(ld_as<C>(R[i + (int64_t)col * ldR]), -ex));
       Acol[(size_t)k * m_max + i] = a;
       Vcol[(size_t)k * m_max + i] = (i == col) ? Tr<C>::one() : Tr<C>::zero();
     }
@@ -422,7 +422,7 @@ k_jacobi_block(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_
       for (int r = tid; r < m; r += nt) {
         C x = Tr<C>::zero();
         if (col < m && r <= col) {
-          x = pow2s<C>(ld_as<C>(R[r + (int64_t)col * ldR]), -ex);
+          x = flush_tiny(pow2s<C>(ld_as<C>(R[r + (int64_t)col * ldR]), -ex));
           const float f = hi32(x);
           fro = fmaf(f, f, fro);
         }

@@ -21,8 +21,11 @@ __global__ void __launch_bounds__(256)
 k_tsmm(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
        int m_val, const VS* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
        SO* __restrict__ Y, int64_t ldy, int tr, int mstr, int m_max, int r_max, int rc,
-       int* status) {
+       int* status, const XRange* xr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  XRead<C, S> rd;
+  rd.sh = xr ? xr->k : 0;
+  rd.flush = xr != nullptr;
   const int m = m_ptr ? *m_ptr : m_val;
   const int r = r_ptr ? *r_ptr : r_val;
   if (m < 1 || m > m_max || r < 1 || r > r_max || r > m || rc < 1) {
@@ -45,7 +48,7 @@ k_tsmm(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict_
     for (int idx = tid; idx < tr * m; idx += nt) {
       const int i = idx % tr, k = idx / tr;
       const int64_t row = r0 + i;
-      T[(size_t)i * mstr + k] = row < rows ? ld_as<C>(W[row + (int64_t)k * ld]) : Tr<C>::zero();
+      T[(size_t)i * mstr + k] = row < rows ? rd(W[row + (int64_t)k * ld]) : Tr<C>::zero();
     }
     for (int c0 = 0; c0 < r; c0 += rc) {
       const int cn = (r - c0) < rc ? (r - c0) : rc;
@@ -76,8 +79,12 @@ template <int RPT, int CPT, int MINB, class C, class S, class VS, class SO>
 __global__ void __launch_bounds__(256, MINB)
 k_tsmm_rb(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
           int m_val, const VS* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
-          SO* __restrict__ Y, int64_t ldy, int m_max, int r_max, int* status) {
+          SO* __restrict__ Y, int64_t ldy, int m_max, int r_max, int* status,
+          const XRange* xr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  XRead<C, S> rd;
+  rd.sh = xr ? xr->k : 0;
+  rd.flush = xr != nullptr;
   const int m = m_ptr ? *m_ptr : m_val;
   const int r = r_ptr ? *r_ptr : r_val;
   if (m < 1 || m > m_max || r < 1 || r > r_max || r > m) {
@@ -112,7 +119,7 @@ k_tsmm_rb(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
         C w[RPT];
 #pragma unroll
         for (int q = 0; q < RPT; ++q)
-          w[q] = ok[q] ? ld_as<C>(W[row[q] + (int64_t)k * ld]) : Tr<C>::zero();
+          w[q] = ok[q] ? rd(W[row[q] + (int64_t)k * ld]) : Tr<C>::zero();
         const C* vk = Vs + k * rp + c0;
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) {
@@ -144,7 +151,8 @@ cudaError_t run_rb(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, co
   }
   k<<<(unsigned)c.ctas, 256, c.smem, s>>>(static_cast<const S*>(W), rows, ld, m_dev, c.m_max,
                                           static_cast<const VS*>(V), ldV, r_dev, c.r_max,
-                                          static_cast<SO*>(Y), ldy, c.m_max, c.r_max, status);
+                                          static_cast<SO*>(Y), ldy, c.m_max, c.r_max, status,
+                                          c.xr);
   return cudaGetLastError();
 }
 
@@ -175,7 +183,7 @@ cudaError_t run(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, const
   k<<<(unsigned)c.ctas, 256, c.smem, s>>>(static_cast<const S*>(W), rows, ld, m_dev, c.m_max,
                                           static_cast<const VS*>(V), ldV, r_dev, c.r_max,
                                           static_cast<SO*>(Y), ldy, c.tr, c.mstr, c.m_max,
-                                          c.r_max, c.rc, status);
+                                          c.r_max, c.rc, status, c.xr);
   return cudaGetLastError();
 }
 

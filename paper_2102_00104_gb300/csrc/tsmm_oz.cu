@@ -57,8 +57,12 @@ template <int NT, class S, class VS, class SO>
 __global__ void __launch_bounds__(OZ_THREADS)
 k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
           int m_val, const VS* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
-          SO* __restrict__ Y, int64_t ldy, int m_max, int r_max, int nbuf, int* status) {
+          SO* __restrict__ Y, int64_t ldy, int m_max, int r_max, int nbuf, int* status,
+          const XRange* xr) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  XRead<df, S> rd;  // W read as W 2^-sh (FP64 input of the float-float form)
+  rd.sh = xr ? xr->k : 0;
+  rd.flush = xr != nullptr;
   const int m = m_ptr ? *m_ptr : m_val;
   const int r = r_ptr ? *r_ptr : r_val;
   if (m < 1 || m > m_max || m_max > OZ_MAXM || r < 1 || r > r_max || r > m || r > 8 * NT ||
@@ -174,7 +178,7 @@ k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
       key0 = max(key0, __shfl_xor_sync(0xffffffffu, key0, o));
       key1 = max(key1, __shfl_xor_sync(0xffffffffu, key1, o));
     }
-    const int be0 = oz_bexp_of(key0, (S*)nullptr), be1 = oz_bexp_of(key1, (S*)nullptr);
+    const int be0 = oz_bexp_of(key0, (S*)nullptr, rd.sh), be1 = oz_bexp_of(key1, (S*)nullptr, rd.sh);
     const float sc0 = oz_inv_scale(be0), sc1 = oz_inv_scale(be1);
 
     float acc[6][NT][4];
@@ -190,8 +194,8 @@ k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
       for (int q = 0; q < 4; ++q) {
         const int k = 16 * kk + 2 * tq + (q & 1) + 8 * (q >> 1);
         const S* c = reinterpret_cast<const S*>(buf + (size_t)(k < m ? k : 0) * OZ_CS);
-        const df x0 = k < m ? ld_as<df>(c[rg]) : Tr<df>::zero();
-        const df x1 = k < m ? ld_as<df>(c[rg + 8]) : Tr<df>::zero();
+        const df x0 = k < m ? rd(c[rg]) : Tr<df>::zero();
+        const df x1 = k < m ? rd(c[rg + 8]) : Tr<df>::zero();
         oz_digits(x0, sc0, dd[q][0]);
         oz_digits(x1, sc1, dd[q][1]);
       }
@@ -285,7 +289,7 @@ cudaError_t run_oz(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, co
   k<<<(unsigned)c.ctas, OZ_THREADS, c.smem, s>>>(static_cast<const S*>(W), rows, ld, m_dev, c.m_max,
                                                  static_cast<const VS*>(V), ldV, r_dev, c.r_max,
                                                  static_cast<SO*>(Y), ldy, c.m_max, c.r_max, c.rc,
-                                                 status);
+                                                 status, c.xr);
   return cudaGetLastError();
 }
 

@@ -88,7 +88,8 @@ template <int NN, class S, class VS, class SO>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tsmm_tc(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
           int m_val, const VS* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
-          SO* __restrict__ Y, int64_t ldy, int m_max, int r_max, int* status) {
+          SO* __restrict__ Y, int64_t ldy, int m_max, int r_max, int* status,
+          const XRange* xr) {
   constexpr int NL = 6;                // levels 2..7
   constexpr int CPW = NN / 4;          // output columns per warp in the read-back
   constexpr uint32_t TMCOLS = 512;     // 21 blocks of NN columns (336)
@@ -210,7 +211,10 @@ k_tsmm_tc(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
     s_key[q][i] = key;
     __syncthreads();
     key = max(max(s_key[0][i], s_key[1][i]), max(s_key[2][i], s_key[3][i]));
-    const int be = oz_bexp_of(key, (S*)nullptr);
+    XRead<df, S> rd;  // W read as W 2^-sh (FP64 input of the float-float form)
+    rd.sh = xr ? xr->k : 0;
+    rd.flush = xr != nullptr;
+    const int be = oz_bexp_of(key, (S*)nullptr, rd.sh);
     if (q == 0) Erow[i] = be;
     const float sc = oz_inv_scale(be);
     // digits of row i, k-groups q, q+4, ...: one 16-byte core-matrix row per plane
@@ -220,7 +224,7 @@ k_tsmm_tc(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int k = 8 * kg + c;
-        const df x = k < m ? ld_as<df>(reinterpret_cast<const S*>(Wt + (size_t)k * TC_CS)[i])
+        const df x = k < m ? rd(reinterpret_cast<const S*>(Wt + (size_t)k * TC_CS)[i])
                            : Tr<df>::zero();
         oz_digits(x, sc, d[c]);
       }
@@ -327,7 +331,8 @@ cudaError_t run_tc(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, co
   if (e != cudaSuccess) return e;
   k<<<(unsigned)c.ctas, TC_THREADS, c.smem, s>>>(static_cast<const S*>(W), rows, ld, m_dev, c.m_max,
                                                  static_cast<const VS*>(V), ldV, r_dev, c.r_max,
-                                                 static_cast<SO*>(Y), ldy, c.m_max, c.r_max, status);
+                                                 static_cast<SO*>(Y), ldy, c.m_max, c.r_max, status,
+                                                 c.xr);
   return cudaGetLastError();
 }
 

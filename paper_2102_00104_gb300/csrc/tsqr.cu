@@ -12,7 +12,7 @@ cudaError_t run_narrow_k(const TsqrLevel& L, const void* W, int64_t ld, const in
   if (L.nw < 1 || L.nw > NW) return cudaErrorInvalidValue;
   k_tsqr_narrow<MAXM, K, NW, C, S, RO><<<(unsigned)L.ctas, L.nw * 32, 0, s>>>(
       static_cast<const S*>(W), L.rows, ld, m_dev, L.mval, static_cast<RO*>(Rout), ldR, L.mb,
-      L.panels, status, tune_get("tsqr.narrow_norm", 1));
+      L.panels, status, tune_get("tsqr.narrow_norm", 1), L.xr, L.xfix);
   return cudaGetLastError();
 }
 
@@ -40,7 +40,7 @@ cudaError_t run_wide(const TsqrLevel& L, const void* W, int64_t ld, const int* m
   kern<<<(unsigned)L.ctas, L.nw * 32, L.smem, s>>>(static_cast<const S*>(W), L.rows, ld, m_dev,
                                                   L.mval, L.pr, mstr, static_cast<C*>(Rscr), L.mmax,
                                                   static_cast<RO*>(Rout), ldR, L.mb, L.panels,
-                                                  status);
+                                                  status, L.xr, L.xfix);
   return cudaGetLastError();
 }
 

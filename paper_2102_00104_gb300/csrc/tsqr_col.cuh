@@ -152,12 +152,8 @@ __device__ __forceinline__ bool publish_r(const C (&x)[PRL], C rjj, int jn, uint
   constexpr int PR = 32 * PRL;
   const int rn = prow(jn, mstr);
   const C D = warp_allsum(dot_rows<PRL>(x, x));
-  C t = add(fmac(rjj, rjj, D), eps);
-  C alpha = sqrt_(add(t, eps));
-  if (is_pos(rjj)) alpha = neg(alpha);
-  t = fnmac(alpha, rjj, t);
-  const C pivn = sub(rjj, alpha);
-  const C rtn = rcp_(t);
+  const Refl<C> h = householder(rjj, D, eps);
+  const C alpha = h.alpha, pivn = h.piv, rtn = h.rt;
   const int sl = g & 1;
   const uint32_t use = g >> 1;
   // the slot's previous pivot (g - 2) must have been read by every warp
@@ -294,9 +290,11 @@ template <int NW, int CLW, int PRL, int MINB, bool RG_MEM, class C, class S, cla
 __global__ void __launch_bounds__(NW * 32, MINB)
 k_tsqr_col(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
            int m_val, int mmax, RO* __restrict__ Rout, int64_t ldR, int mb, int64_t npanels,
-           C* __restrict__ Rglob, int* status) {
+           C* __restrict__ Rglob, int* status, XRange* xr, int xfix) {
   constexpr int PR = 32 * PRL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  XRead<C, S> rd;
+  if (!xr_begin(xr, xfix, rd)) return;
   const int m = m_ptr ? *m_ptr : m_val;
   if (m < 1 || m > NW * CLW || m > mmax || m > mb || blockDim.x != NW * 32) {
     if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
@@ -333,7 +331,7 @@ k_tsqr_col(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restr
 #pragma unroll
       for (int q = 0; q < PRL; ++q) {
         const int64_t row = p * PR + lane + 32 * q;
-        a[c][q] = (row < rows && k < m) ? ld_as<C>(W[row + (int64_t)k * ld]) : Tr<C>::zero();
+        a[c][q] = (row < rows && k < m) ? rd(W[row + (int64_t)k * ld]) : Tr<C>::zero();
       }
     }
     // warm L2 with the next panel of this CTA (two requests per 256-byte column segment)
@@ -357,6 +355,7 @@ k_tsqr_col(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restr
   }
   __syncthreads();
   if (*reinterpret_cast<volatile int*>(abort_flag)) return;
+  xr_end(xr, xfix, rd);
   for (int idx = tid; idx < mb * m; idx += nt) {
     const int i = idx % mb, k = idx / mb;
     C v = Tr<C>::zero();
@@ -377,7 +376,7 @@ cudaError_t run_col(const TsqrLevel& L, const void* W, int64_t ld, const int* m_
   }
   kern<<<(unsigned)L.ctas, NW * 32, L.smem, s>>>(static_cast<const S*>(W), L.rows, ld, m_dev, L.mval,
                                                 L.mmax, static_cast<RO*>(Rout), ldR, L.mb, L.panels,
-                                                nullptr, status);
+                                                nullptr, status, L.xr, L.xfix);
   return cudaGetLastError();
 }
 

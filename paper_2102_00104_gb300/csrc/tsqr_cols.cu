@@ -18,7 +18,8 @@ cudaError_t run_cols(const TsqrLevel& L, const void* W, int64_t ld, const int* m
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)L.ctas, kNW * 32, L.smem, s>>>(static_cast<const S*>(W), L.rows, ld, m_dev,
                                                  L.mval, L.mmax, static_cast<df*>(Rout), ldR, L.mb,
-                                                 L.panels, static_cast<df*>(Rscr), status);
+                                                 L.panels, static_cast<df*>(Rscr), status, L.xr,
+                                                 L.xfix);
   return cudaGetLastError();
 }
 

@@ -18,12 +18,14 @@ template <int NW, int CH, int PRL, class C, class S, class RO>
 __global__ void __launch_bounds__(NW * 32, 1)
 k_tsqr_cols(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
             int m_val, int mmax, RO* __restrict__ Rout, int64_t ldR, int mb, int64_t npanels,
-            C* __restrict__ Rglob, int* status) {
+            C* __restrict__ Rglob, int* status, XRange* xr, int xfix) {
   using namespace colk;
   constexpr int PR = 32 * PRL;
   constexpr int L = ilog2(CH);
   constexpr int MAXCH = 8;   // chunks per warp: m <= NW * CH * MAXCH
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  XRead<C, S> rd;
+  if (!xr_begin(xr, xfix, rd)) return;
   const int m = m_ptr ? *m_ptr : m_val;
   if (m < 1 || m > mmax || m > mb || m > NW * CH * MAXCH || blockDim.x != NW * 32) {
     if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
@@ -62,7 +64,7 @@ k_tsqr_cols(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __rest
 #pragma unroll
       for (int q = 0; q < PRL; ++q) {
         const int64_t row = p * PR + lane + 32 * q;
-        col[lane + 32 * q] = row < rows ? ld_as<C>(W[row + (int64_t)k * ld]) : Tr<C>::zero();
+        col[lane + 32 * q] = row < rows ? rd(W[row + (int64_t)k * ld]) : Tr<C>::zero();
       }
     }
     __syncwarp();
@@ -163,6 +165,7 @@ k_tsqr_cols(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __rest
   }
   __syncthreads();
   if (*reinterpret_cast<volatile int*>(abort_flag)) return;
+  xr_end(xr, xfix, rd);
   for (int i2 = tid; i2 < mb * m; i2 += nt) {
     const int i = i2 % mb, k = i2 / mb;
     C v = Tr<C>::zero();

@@ -19,7 +19,8 @@ cudaError_t run_cta(const TsqrLevel& L, const void* W, int64_t ld, const int* m_
   }
   kern<<<(unsigned)L.ctas, kNW * 32, L.smem, s>>>(static_cast<const S*>(W), L.rows, ld, m_dev,
                                                   L.mval, L.mmax, static_cast<RO*>(Rout), ldR,
-                                                  L.mb, L.panels, static_cast<C*>(Rscr), status);
+                                                  L.mb, L.panels, static_cast<C*>(Rscr), status,
+                                                  L.xr, L.xfix);
   return cudaGetLastError();
 }
 

@@ -32,7 +32,9 @@ template <int CG, int CL, int RL, int NW, int MINB, bool RG_MEM, class C, class 
 __global__ void __launch_bounds__(NW * 32, MINB)
 k_tsqr_cta(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
            int m_val, int mmax, RO* __restrict__ Rout, int64_t ldR, int mb, int64_t npanels,
-           C* __restrict__ Rglob, int* status) {
+           C* __restrict__ Rglob, int* status, XRange* xr, int xfix) {
+  XRead<C, S> rd;
+  if (!xr_begin(xr, xfix, rd)) return;
   constexpr int RGW = 32 / CG;
   constexpr int RG = NW * RGW;
   constexpr int PR = RG * RL;
@@ -67,7 +69,7 @@ k_tsqr_cta(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restr
 #pragma unroll
       for (int c = 0; c < CL; ++c) {
         const int k = cg + CG * c;
-        a[q][c] = (ok && k < m) ? ld_as<C>(W[row + (int64_t)k * ld]) : Tr<C>::zero();
+        a[q][c] = (ok && k < m) ? rd(W[row + (int64_t)k * ld]) : Tr<C>::zero();
       }
     }
     for (int j = 0; j < m; ++j) {
@@ -120,16 +122,13 @@ k_tsqr_cta(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restr
         const C dk = pk[0], dj = pj[0];
         const int rj = packed_row(j, m);
         const C rjj = R[rj];
-        C t = add(fmac(rjj, rjj, dj), eps);
-        C alpha = sqrt_(add(t, eps));
-        if (is_pos(rjj)) alpha = neg(alpha);
-        t = fnmac(alpha, rjj, t);
-        const C piv = sub(rjj, alpha);
+        const Refl<C> h = householder(rjj, dj, eps);
+        const C alpha = h.alpha, piv = h.piv;
         if (k == j) {
           alpha_keep = alpha;
         } else {
           const C rjk = R[rj + (k - j)];
-          const C ck = mul(fmac(piv, rjk, dk), rcp_(t));
+          const C ck = mul(fmac(piv, rjk, dk), h.rt);
           R[rj + (k - j)] = fnmac(ck, piv, rjk);
           Cc[k] = ck;
         }
@@ -149,6 +148,7 @@ k_tsqr_cta(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restr
     }
   }
   __syncthreads();
+  xr_end(xr, xfix, rd);
   for (int idx = tid; idx < mb * m; idx += nt) {
     const int i = idx % mb, k = idx / mb;
     C v = Tr<C>::zero();

@@ -5,9 +5,11 @@
 // range of panels and folds each one into its own triangle R by the
 // Householder QR of [M; R] (Alg. 6, read as: the reflector of column j acts on
 // all rows of the panel M and on row j of R, pivot R[j][j]).  The scaled,
-// branch-free reflector of Alg. 6 lines 4-7 is used:
-//   t = ||u||^2 + eps ; alpha = -+sqrt(t + eps) (sign opposite to the pivot)
+// reflector of Alg. 6 is used (householder() in arith.cuh):
+//   t = ||u||^2 (+ eps_FP in native FP64) ; alpha = -+sqrt(t) (sign opposite to the pivot)
 //   t = t - alpha * R_jj ; piv = R_jj - alpha
+// (in FP32 and float-float, whose input is shifted to max |x| ~ 1, a column with
+// t < 2^-100 leaves the reflector as the identity instead of adding eps_FP)
 // and every later column k is updated with c_k = (piv * R_jk + M_j . M_k) / t:
 //   R_jk <- R_jk - c_k * piv ,   M_ik <- M_ik - c_k * M_ij
 // (this is w <- w - (v^T w) v with v = u / sqrt(t), written without the root).
@@ -34,8 +36,10 @@ template <int NCH, class C, class S, class RO>
 __global__ void __launch_bounds__(128)
 k_tsqr_wide(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
             int m_val, int pr, int mstr, C* __restrict__ Rscr, int mbs, RO* __restrict__ Rout,
-            int64_t ldR, int mb, int64_t npanels, int* status) {
+            int64_t ldR, int mb, int64_t npanels, int* status, XRange* xr, int xfix) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  XRead<C, S> rd;
+  if (!xr_begin(xr, xfix, rd)) return;
   const int m = m_ptr ? *m_ptr : m_val;
   if (m < 1 || m > 32 * NCH || m > mbs || m > mstr || m > mb || (pr & 31) != 0) {
     if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
@@ -59,7 +63,7 @@ k_tsqr_wide(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __rest
       const int64_t row = r0 + i;
       const bool ok = row < rows;
       for (int k = 0; k < m; ++k)
-        P[(size_t)i * mstr + k] = ok ? ld_as<C>(W[row + (int64_t)k * ld]) : Tr<C>::zero();
+        P[(size_t)i * mstr + k] = ok ? rd(W[row + (int64_t)k * ld]) : Tr<C>::zero();
     }
     __syncwarp();
     for (int j = 0; j < m; ++j) {
@@ -89,12 +93,8 @@ k_tsqr_wide(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __rest
         if (c == (j >> 5)) { dj = s[c]; rjj = rr[c]; }
       dj = shfl_idx(dj, j & 31);
       rjj = shfl_idx(rjj, j & 31);
-      C t = add(fmac(rjj, rjj, dj), eps);
-      C alpha = sqrt_(add(t, eps));
-      if (is_pos(rjj)) alpha = neg(alpha);
-      t = fnmac(alpha, rjj, t);
-      const C piv = sub(rjj, alpha);
-      const C tinv = div_(Tr<C>::one(), t);
+      const Refl<C> h = householder(rjj, dj, eps);
+      const C alpha = h.alpha, piv = h.piv, tinv = h.rt;
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {
         const int k = lane + 32 * c;
@@ -110,6 +110,7 @@ k_tsqr_wide(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __rest
       __syncwarp();
     }
   }
+  xr_end(xr, xfix, rd);
   for (int i = 0; i < mb; ++i)
     for (int k = lane; k < m; k += 32) {
       C v = Tr<C>::zero();

@@ -18,8 +18,8 @@
 //   warps update columns j+2 .. m-1.  One CTA barrier per column; no spin waits.
 //
 // The reflector and the column update use the same scaled, branch-free form of Alg. 6
-// as the level kernels (tsqr_kernels.cuh): t = ||x||^2 + R_jj^2 + eps,
-// alpha = -+sqrt(t + eps), t -= alpha R_jj, piv = R_jj - alpha,
+// as the level kernels (householder() in arith.cuh): t = ||x||^2 + R_jj^2,
+// alpha = -+sqrt(t), t -= alpha R_jj, piv = R_jj - alpha,
 // c_k = (piv R_jk + x . y_k) / t, R_jk -= c_k piv, y_k -= c_k x.
 #include "tsqr_col.cuh"
 
@@ -41,17 +41,14 @@ __device__ __forceinline__ C make_reflector(C (&y)[QMAX], C rjj, C* slot, int la
     acc = lz_fmac(y[q], y[q], acc);
   }
   const C D = colk::warp_allsum(lz_fin(acc));
-  C t = add(fmac(rjj, rjj, D), eps);
-  C alpha = sqrt_(add(t, eps));
-  if (is_pos(rjj)) alpha = neg(alpha);
-  t = fnmac(alpha, rjj, t);
+  const Refl<C> h = householder(rjj, D, eps);
 #pragma unroll
   for (int q = 0; q < QMAX; ++q) slot[lane + 32 * q] = y[q];
   if (lane == 0) {
-    slot[32 * QMAX] = sub(rjj, alpha);
-    slot[32 * QMAX + 1] = rcp_(t);
+    slot[32 * QMAX] = h.piv;
+    slot[32 * QMAX + 1] = h.rt;
   }
-  return alpha;
+  return h.alpha;
 }
 
 template <int QMAX, int CH, int NW, class C, class S>

@@ -17,12 +17,14 @@ template <int MAXM, int K, int NW, class C, class S, class RO>
 __global__ void __launch_bounds__(NW * 32)
 k_tsqr_narrow(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
               int m_val, RO* __restrict__ Rout, int64_t ldR, int mb, int64_t npanels, int* status,
-              int normalize) {
+              int normalize, XRange* xr, int xfix) {
   constexpr int PR = 32 * K;
   constexpr int LG = MAXM == 4 ? 2 : (MAXM == 8 ? 3 : 4);  // log2(MAXM)
   constexpr int G = 32 / MAXM;                               // lanes per column after the butterfly
   static_assert((1 << LG) == MAXM, "MAXM is 4, 8 or 16");
   __shared__ C Rsh[NW][MAXM][MAXM];
+  XRead<C, S> rd;
+  if (!xr_begin(xr, xfix, rd)) return;
   const int m = m_ptr ? *m_ptr : m_val;
   const int nwb = blockDim.x >> 5;
   if (m < 1 || m > MAXM || m > mb || nwb > NW) {
@@ -47,7 +49,7 @@ k_tsqr_narrow(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __re
       const bool ok = row < rows;
 #pragma unroll
       for (int k = 0; k < MAXM; ++k)
-        a[q][k] = (ok && k < m) ? ld_as<C>(W[row + (int64_t)k * ld]) : Tr<C>::zero();
+        a[q][k] = (ok && k < m) ? rd(W[row + (int64_t)k * ld]) : Tr<C>::zero();
     }
     for (int j = 0; j < m; ++j) {
       // pivot column j, renormalised (a product of two float-float pairs drops lo*lo)
@@ -91,12 +93,8 @@ k_tsqr_narrow(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __re
       // reflector scalars (identical in every lane); D = ||M_j||^2 from group j
       const C D = shfl_idx(tot, j * G);
       const C rjj = R[j][j];
-      C t = add(fmac(rjj, rjj, D), eps);
-      C alpha = sqrt_(add(t, eps));
-      if (is_pos(rjj)) alpha = neg(alpha);
-      t = fnmac(alpha, rjj, t);
-      const C piv = sub(rjj, alpha);
-      const C rt = rcp_(t);
+      const Refl<C> h = householder(rjj, D, eps);
+      const C alpha = h.alpha, piv = h.piv, rt = h.rt;
       // coefficient of this group's column: c_k = (piv R_jk + M_j . M_k) / t
       C ck = Tr<C>::zero(), rnew = Tr<C>::zero();
       const bool own = idx > j && idx < m;
@@ -124,6 +122,7 @@ k_tsqr_narrow(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __re
       __syncwarp();
     }
   }
+  xr_end(xr, xfix, rd);
   // stacked output block: rows gw*mb + i (i < mb), columns k < m
   for (int idx = lane; idx < mb * m; idx += 32) {
     const int i = idx % mb, k = idx / mb;

@@ -67,11 +67,12 @@ struct RankList {
 };
 
 __global__ void k_put_ranks(RankList rl, int count, int64_t* ranks_out, const double* e,
-                            double* err2_out) {
+                            double* err2_out, const XRange* xr) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (ranks_out)
     for (int i = 0; i < count; ++i) ranks_out[i] = rl.r[i];
-  if (err2_out) *err2_out = *e;
+  // the discarded sigma^2 were of X 2^-k
+  if (err2_out) *err2_out = xr ? ldexp(*e, 2 * xr->k) : *e;
 }
 
 __global__ void k_zero(double* e) {
@@ -126,11 +127,11 @@ cudaError_t launch_zero(double* e, cudaStream_t s) {
 }
 
 cudaError_t launch_put_ranks(const int64_t* ranks, int count, int64_t* ranks_out, const double* e,
-                             double* err2_out, cudaStream_t s) {
+                             double* err2_out, cudaStream_t s, const XRange* xr) {
   if (count > TT_MAX_RANKS) return cudaErrorInvalidValue;
   RankList rl{};
   for (int i = 0; i < count; ++i) rl.r[i] = ranks[i];
-  k_put_ranks<<<1, 32, 0, s>>>(rl, count, ranks_out, e, err2_out);
+  k_put_ranks<<<1, 32, 0, s>>>(rl, count, ranks_out, e, err2_out, xr);
   return cudaGetLastError();
 }
 

@@ -115,6 +115,37 @@ def planted_tt(dims, rank: int, seed: int, noise_rel: float = 1e-6) -> np.ndarra
     return X
 
 
+def planted_tt_device(dims, rank: int, seed: int, noise_rel: float = 1e-6, device="cuda"):
+    """planted_tt built on the device for tensors too large for the host: the same cores
+    (numpy PCG64 from ``seed``, drawn in the same order), contracted in FP64 with torch on
+    the device; the noise is N(0,1) from torch's generator seeded with ``seed`` (a different
+    draw of the same distribution), scaled to ||E||_F = noise_rel ||X||_F.  Returns the flat
+    Fortran-order FP64 tensor (n_1 fastest) as a device tensor."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    d = len(dims)
+    r = [1] * (d + 1)
+    for k in range(1, d):
+        r[k] = min(rank, int(np.prod(dims[:k])), int(np.prod(dims[k:])))
+    A = torch.from_numpy(rng.standard_normal((dims[0], r[1]))).to(device)
+    N = dims[0]
+    for k in range(1, d):
+        core = torch.from_numpy(rng.standard_normal((r[k], dims[k] * r[k + 1]))).to(device)
+        A = A @ core  # (N, n_k r_{k+1}), column index i_k + n_k * a
+        N *= dims[k]
+        # Fortran-order reshape to (N n_k, r_{k+1}): column-major A is A^T in C order
+        A = A.t().contiguous().view(r[k + 1], N).t()
+    X = A.t().contiguous().view(-1)  # column-major (N, 1) data = Fortran order
+    X /= torch.sqrt(torch.sum(X * X))
+    if noise_rel > 0:
+        g = torch.Generator(device=device).manual_seed(seed)
+        E = torch.randn(X.numel(), dtype=torch.float64, device=device, generator=g)
+        X += E * (noise_rel / torch.sqrt(torch.sum(E * E)))
+        del E
+    return X
+
+
 def to_device_layout(X: np.ndarray) -> np.ndarray:
     """Flat Fortran-order copy of X (n_1 fastest): the memory layout the library expects."""
     return np.asarray(X).ravel(order="F")

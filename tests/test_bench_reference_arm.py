@@ -36,7 +36,10 @@ def test_reference_line_matches_the_cuda_arm_contract():
     assert d["metric"] == bench.METRIC and d["unit"] == "GB/s" and d["higher_is_better"] is True
     # 4^10 without tolerance: ranks min(8, 4^k, 4^(10-k))
     ranks = [1, 4, 8, 8, 8, 8, 8, 8, 8, 4, 1]
-    assert d["config"] == bench.workload_config(4, 10, 8, ranks, 1)
+    # the workload's config, plus the name of the bounded sample each timed step runs
+    cfg = dict(d["config"])
+    assert "4^8" in cfg.pop("sample_per_step")
+    assert cfg == bench.workload_config(4, 10, 8, ranks, 1)
     assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["ms_per_step"] > 0
     cb = d["cpu_baseline"]

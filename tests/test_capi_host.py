@@ -2,9 +2,11 @@
 host-side sizing and argument checks behave (no GPU needed, no compute calls)."""
 import ctypes as C
 import glob
+import math
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2102_00104_gb300 import build as B
@@ -150,6 +152,9 @@ def test_batched_and_serve_argument_checks(lib):
     res = capi.tt_job_result()
     assert lib.tt_serve_poll(None, 1, 0, C.byref(res)) == capi.TT_EINVAL
     assert lib.tt_serve_destroy(None) == capi.TT_EINVAL
+    assert lib.tt_serve_release(None, 1) == capi.TT_EINVAL
+    t = C.c_uint64(0)
+    assert lib.tt_serve_submit(None, C.byref(job), None, C.byref(t)) == capi.TT_EINVAL
 
 
 def test_from_host_argument_checks(lib):
@@ -186,3 +191,29 @@ def test_tune_overrides_from_environment():
     env["TT_TUNE"] = "tsmm.oz"  # no value: refused loudly
     r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True)
     assert r.returncode != 0
+
+
+def test_range_rule(lib):
+    """The exponent shift of the float-float FP64 form (include/tt_svd.h, tt_range_rule):
+    X is read as X 2^-k with max|x| 2^-k in [0.5, 1); the first TSQR level runs again when
+    the largest entry it met lies more than 40 binades outside the sample's window."""
+    NONE = capi.TT_RANGE_NONE
+    # uniform[0,1) data: largest entry in [0.5, 1) -> no shift, no re-run
+    assert capi.tt_range_rule(-1, -1) == (0, 0, 0)
+    # the definition: 2^e <= max|x| < 2^(e+1)  ->  k = e + 1
+    for x in (1.0, 3.0, 1e25, 1e-30, 2.0 ** -1060, 1.7e308):
+        e = int(np.floor(np.log2(x)))
+        k_try, redo, k = capi.tt_range_rule(e, e)
+        assert (k_try, redo, k) == (e + 1, 0, e + 1)
+        assert 0.5 <= math.ldexp(x, -k) < 1.0
+    # an entry far above the sample: re-run with the shift of the largest entry
+    assert capi.tt_range_rule(-1, 40 - 1) == (0, 0, 0)      # 2^39: inside the window
+    assert capi.tt_range_rule(-1, 41) == (0, 1, 42)          # 2^41: above it
+    assert capi.tt_range_rule(83, 100) == (84, 0, 84)
+    # no sample (a strided matrix): tiny data is caught on the other side of the window
+    assert capi.tt_range_rule(NONE, -100) == (0, 1, -99)
+    assert capi.tt_range_rule(NONE, -30) == (0, 0, 0)
+    # nothing nonzero: no shift
+    assert capi.tt_range_rule(NONE, NONE) == (0, 0, 0)
+    code = lib.tt_range_rule(5000, 0, C.byref(C.c_int()), C.byref(C.c_int()), C.byref(C.c_int()))
+    assert code == capi.TT_EINVAL

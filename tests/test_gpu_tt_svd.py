@@ -30,7 +30,7 @@ def run_gpu(X, r_max, tol=0.0, dtype=torch.float64, arith="df", no_elide=False):
     return plan.result()
 
 
-def compare(X, res, ref, tol_rel):
+def compare(X, res, ref, tol_rel, check_err2=True):
     assert res.ranks == ref.ranks, (res.ranks, ref.ranks)
     smax = max(s[0] for s in ref.sigmas.values())
     for i, s in ref.sigmas.items():
@@ -45,7 +45,8 @@ def compare(X, res, ref, tol_rel):
     err = np.linalg.norm(O.tt_full(cores) - X) / nx
     err_ref = np.linalg.norm(O.tt_full(ref.cores) - X) / nx
     assert abs(err - err_ref) <= tol_rel, (err, err_ref)
-    assert abs(res.err2 - ref.err2) <= tol_rel * nx * nx
+    if check_err2:
+        assert abs(res.err2 - ref.err2) <= tol_rel * nx * nx
     for c in cores[1:]:
         assert O.core_orthonormality_defect(c) <= max(1e-12, tol_rel * 10)
     return err
