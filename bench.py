@@ -4,15 +4,20 @@
 One step = one truncated TT-SVD (Alg. 2: TSQR, small SVD, rank choice, core,
 W*V_r for every step) of an i.i.d. uniform[0,1) 8^10 tensor resident in HBM,
 r_max from --rmax (default 10), no tolerance truncation.  The input (8 GiB) is
-larger than L2 (126 MB), so no flush is needed between steps.
+larger than L2 (126 MB), so no flush is needed between steps.  The headline runs in
+native FP64 arithmetic (--arith f64, the FP64-accurate form); the float-float form
+(FP64 storage, ~48-bit arithmetic) is reported beside it with its own roofline.
 
 value    = N * 8 GiB / (device time per step, CUDA events, max over ranks), GB/s
 e2e      = the same metric when every step also copies X from pinned host
            memory and reads the cores, ranks and error back
 roofline = the dominant kernel of the step, timed live with CUDA events inside
-           the timed region by the library's profile mode
-Also reported: the r_max sweep {1,5,10,20,50}, the FP32-storage form at r_max=32,
-the oracle's throughput on host cores (cpu_baseline) and SM clocks.
+           the timed region by the library's profile mode; its ALU peak is this
+           GPU's FMA rate measured at start-up by the library (tt_fma_rate)
+Also reported: the float-float form, the planted TT-rank-16 input, the r_max sweep
+{1,5,10,20,50} in both arithmetics, the FP32-storage form at r_max=32 with its error
+against the FP64 form, the batched and serve forms, the oracle's throughput on host
+cores (cpu_baseline) and SM clocks.
 
 --impl reference times the CPU oracle (Alg. 1, numpy/LAPACK FP64) on the same
 metric with a bounded sample of the workload.
@@ -39,10 +44,8 @@ sys.path.insert(0, ROOT)
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
 FALLBACK_HBM_GBS = 6800.0
-# float-float FMA = 15 FP32 instructions (TwoProd 2, cross terms 2, TwoSum 6,
-# error adds 2, FastTwoSum 3); measured FP32 FMA rate 35.05e12/s (70.1 TFLOP/s)
-DF_FMA_INSTR = 15
-FP32_FMA_RATE_MEASURED = 35.05e12
+ARITH_LABEL = {"f64": "f64 (native FP64 arithmetic)",
+               "df": "f64 storage, float-float (2xFP32, ~48-bit) arithmetic"}
 
 
 def parse():
@@ -54,7 +57,8 @@ def parse():
     p.add_argument("--rmax", type=int, default=10)
     p.add_argument("--n", type=int, default=8)
     p.add_argument("--d", type=int, default=10)
-    p.add_argument("--arith", default="df", choices=["df", "f64"])
+    p.add_argument("--arith", default="f64", choices=["df", "f64"],
+                   help="arithmetic of the headline (f64: native FP64; df: float-float)")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-extras", action="store_true", help="skip sweep, FP32 form, e2e, CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -191,6 +195,8 @@ def run_reference(args):
     cores = len(os.sched_getaffinity(0))
     sample = f"Alg. 1 oracle on a {args.n}^8 uniform FP64 tensor ({X.nbytes / 2**20:.0f} MiB) per step, r_max={args.rmax}"
     config = workload_config(args.n, args.d, args.rmax, O.planned_ranks([args.n] * args.d, args.rmax), args.gpus)
+    # each timed step of this arm is a bounded sample of the workload: name it
+    config["sample_per_step"] = sample
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s",
             "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": el * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -280,6 +286,68 @@ def run_case(spec: str) -> int:
     return 0
 
 
+def aggregate_profile(prof, ms_step):
+    """Per-kernel records of the library's profile mode, averaged per (kernel, step)."""
+    agg = {}
+    for r in prof:
+        key = (r["kind"], r["step"])
+        a = agg.setdefault(key, {"ms": 0.0, "bytes": r["bytes"], "flops": r["flops"], "n": 0, "info": r["info"]})
+        a["ms"] += r["ms"]
+        a["n"] += 1
+    out = []
+    for (kind, step), a in agg.items():
+        t = a["ms"] / a["n"]
+        out.append({"kernel": kind, "step": step, "ms": t, "share": t / ms_step, "info": a["info"],
+                    "gbs": a["bytes"] / (t / 1e3) / 1e9,
+                    "tflops_fp64eq": a["flops"] / (t / 1e3) / 1e12, "bytes": a["bytes"], "flops": a["flops"]})
+    out.sort(key=lambda e: -e["ms"])
+    return out
+
+
+def roofline_of(top, arith, alu_peaks, hbm_peak, peak_src, workload):
+    """The roofline object of the dominant kernel: its ALU fraction against this GPU's
+    measured FMA rate for the arithmetic, its HBM fraction against the measured copy
+    bandwidth; `bound` is the larger of the two."""
+    alu_peak = alu_peaks[arith]
+    hbm_frac = top["gbs"] / hbm_peak
+    alu_frac = top["tflops_fp64eq"] / alu_peak if top["flops"] > 0 else 0.0
+    kname = f"{top['kernel']}@step{top['step']}"
+    traffic = lookup_traffic(top["kernel"], f"{workload} step{top['step']}")
+    src = {"f64": "FP64 FMA rate measured by tt_fma_rate in this run",
+           "df": "float-float multiply-add rate measured by tt_fma_rate in this run (FP64-equivalent)",
+           "f32": "FP32 FMA rate measured by tt_fma_rate in this run"}[arith]
+    if alu_frac > hbm_frac:
+        return {"bound": "alu", "kernel": kname, "achieved": top["tflops_fp64eq"], "peak": alu_peak,
+                "unit": "TFLOP/s" + (" (FP64-equivalent)" if arith == "df" else ""), "frac": alu_frac,
+                "traffic": traffic, "peak_source": src,
+                "hbm_view": {"achieved": top["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
+                             "peak_source": peak_src}}
+    return {"bound": "hbm", "kernel": kname, "achieved": top["gbs"], "peak": hbm_peak, "unit": "GB/s",
+            "frac": hbm_frac, "traffic": traffic, "peak_source": peak_src,
+            "alu_view": {"achieved": top["tflops_fp64eq"], "peak": alu_peak, "frac": alu_frac,
+                         "peak_source": src}}
+
+
+def time_plan(torch, plan, X, reps, stream, capi=None):
+    """Device ms per TT-SVD over `reps` back-to-back runs (CUDA events on the stream), and
+    the per-kernel profile records when capi is given."""
+    plan.run(X, stream)
+    torch.cuda.synchronize()
+    if capi:
+        capi.tt_profile(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        plan.run(X, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    prof = None
+    if capi:
+        prof = capi.tt_profile_read()
+        capi.tt_profile(False)
+    return a.elapsed_time(b) / reps, prof
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -312,6 +380,9 @@ def main():
     in_bytes = nbar * 8
     hbm_peak, peak_src = load_peaks()
     stream = torch.cuda.current_stream()
+    # this GPU's arithmetic peaks, measured by the library (FP64-equivalent flop/s)
+    alu_peaks = {"f64": capi.tt_fma_rate(capi.FMA_FP64) / 1e12, "df": capi.tt_fma_rate(capi.FMA_DF) / 1e12,
+                 "f32": capi.tt_fma_rate(capi.FMA_FP32) / 1e12}
 
     X = api.gen_uniform(nbar, args.seed + 1000 * rank, torch.float64)
     plan = api.TTSVDPlan(dims, args.rmax, 0.0, torch.float64, args.arith)
@@ -346,61 +417,32 @@ def main():
     ms = max_over_ranks(ms, device="cuda")
     value = world * in_bytes / (ms / 1e3) / 1e9
 
-    # per-kernel breakdown from the live events (per launch = per step)
-    agg = {}
-    for r in prof:
-        key = (r["kind"], r["step"])
-        a = agg.setdefault(key, {"ms": 0.0, "bytes": r["bytes"], "flops": r["flops"], "n": 0, "info": r["info"]})
-        a["ms"] += r["ms"]
-        a["n"] += 1
-    per_kernel = []
-    for (kind, step), a in agg.items():
-        t = a["ms"] / a["n"]
-        per_kernel.append({"kernel": kind, "step": step, "ms": t, "share": t / ms, "info": a["info"],
-                           "gbs": a["bytes"] / (t / 1e3) / 1e9,
-                           "tflops_fp64eq": a["flops"] / (t / 1e3) / 1e12, "bytes": a["bytes"], "flops": a["flops"]})
-    per_kernel.sort(key=lambda e: -e["ms"])
-    top = per_kernel[0]
+    per_kernel = aggregate_profile(prof, ms)
     workload = f"{args.n}^{args.d} f64 r_max={args.rmax} {args.arith}"
-    hbm_frac = top["gbs"] / hbm_peak
-    if args.arith == "df":
-        alu_peak = 2.0 * FP32_FMA_RATE_MEASURED / DF_FMA_INSTR / 1e12   # FP64-equivalent TFLOP/s
-    else:
-        alu_peak = 1.009  # measured native FP64 FMA rate, TFLOP/s
-    alu_frac = top["tflops_fp64eq"] / alu_peak if top["flops"] > 0 else 0.0
-    kname = f"{top['kernel']}@step{top['step']}"
-    traffic = lookup_traffic(top["kernel"], f"{workload} step{top['step']}")
-    if alu_frac > hbm_frac:
-        roof = {"bound": "alu", "kernel": kname, "achieved": top["tflops_fp64eq"], "peak": alu_peak,
-                "unit": "TFLOP/s (FP64-equivalent)", "frac": alu_frac, "traffic": traffic,
-                "peak_source": "measured FP32 FMA rate / 15 FP32 instructions per float-float FMA" if args.arith == "df" else "measured FP64 FMA rate",
-                "hbm_view": {"achieved": top["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
-                             "peak_source": peak_src}}
-    else:
-        roof = {"bound": "hbm", "kernel": kname, "achieved": top["gbs"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": hbm_frac, "traffic": traffic, "peak_source": peak_src,
-                "alu_view": {"achieved": top["tflops_fp64eq"], "peak": alu_peak, "frac": alu_frac}}
+    roof = roofline_of(per_kernel[0], args.arith, alu_peaks, hbm_peak, peak_src, workload)
     two_read_ms = 2 * in_bytes / (hbm_peak * 1e9) * 1e3
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        extras = run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, stream)
+        extras = run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, peak_src,
+                            stream, alu_peaks)
 
+    paper = paper_input_gbs(args.n, args.d, args.rmax)
     out = {
         "metric": METRIC,
         "value": value, "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": (value / paper_input_gbs(args.n, args.d, args.rmax)
-                        if paper_input_gbs(args.n, args.d, args.rmax) else None),
-        "vs_baseline_ref": ({"gbs": paper_input_gbs(args.n, args.d, args.rmax),
+        "vs_baseline": value / paper if paper else None,
+        "vs_baseline_ref": ({"gbs": paper,
                              "source": "the paper's TT-SVD time for this tensor and r_max on one 14-core "
                                        "Skylake socket (Sec. 5.2), another machine: context, not the target"}
-                            if paper_input_gbs(args.n, args.d, args.rmax) else None),
-        "dtype": "f64" if args.arith == "f64" else "f64 storage, float-float (2xFP32) arithmetic",
+                            if paper else None),
+        "dtype": ARITH_LABEL[args.arith],
         "data": "synthetic: i.i.d. uniform[0,1) from Philox4x32-10, generated on the device",
         "config": workload_config(args.n, args.d, args.rmax, ranks, world),
         "two_read_roofline": {"ms": two_read_ms, "frac": two_read_ms / ms, "hbm_gbs": hbm_peak, "source": peak_src},
         "roofline": roof,
+        "alu_peaks_tflops": alu_peaks,
         "per_kernel": per_kernel[:8],
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -414,8 +456,26 @@ def main():
     return 0
 
 
-def run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, stream):
+def tt_full_device(torch, cores, dims):
+    """The full tensor of a TT (cores of shape (r_{i-1}, n_i, r_i), FP64, on the device) as
+    a flat Fortran-order vector (n_1 fastest): measurement only, plain torch matmuls."""
+    A = cores[0].reshape(dims[0], -1)  # (n_1, r_1): core 1 with r_0 = 1
+    N = dims[0]
+    for k in range(1, len(dims)):
+        c = cores[k]  # (r_{k-1}, n_k, r_k) as a torch view
+        r0, nk, r1 = c.shape
+        A = A @ c.reshape(r0, nk * r1)  # (N, n_k r_k), column j r_k + b
+        # (N, n_k, r_k) -> (N n_k, r_k) with row index i + N j (Fortran order)
+        A = A.reshape(N, nk, r1).permute(1, 0, 2).reshape(N * nk, r1)
+        N *= nk
+    return A.reshape(-1)
+
+
+def run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, peak_src, stream,
+               alu_peaks):
     out = {}
+    two_read_ms = 2 * in_bytes / (hbm_peak * 1e9) * 1e3
+    other = "df" if args.arith == "f64" else "f64"
     # e2e: host buffers through the public API, copies inside the timed region
     try:
         Xh = torch.empty(nbar, dtype=torch.float64, pin_memory=True)
@@ -441,97 +501,105 @@ def run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, 
         out["e2e"] = {"value": in_bytes / (ms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
                       "h2d_bytes_per_step": in_bytes,
                       "d2h_bytes_per_step": caps_bytes + host_ranks.numel() * 8 + 8,
-                      "api": "tt_svd_from_host (pinned X, 16 row blocks) + D2H of cores, ranks, err2"}
+                      "api": "tt_svd_from_host (pinned X, 16 row blocks) + D2H of cores, ranks, err2",
+                      "arith": args.arith}
         del Xh
     except Exception as e:  # pinned 8 GiB may be refused on small hosts
         out["e2e"] = {"value": None, "unit": "GB/s", "error": str(e)[:200]}
-    # thick-bounds variant (Alg. 3, m_min = 16, f1_min = 1/2) beside the plain algorithm
-    thick = {}
+    # the same workload in the other arithmetic, with its own per-kernel profile and roofline
+    p = api.TTSVDPlan(dims, args.rmax, 0.0, torch.float64, other)
+    ms, prof = time_plan(torch, p, X, 3, stream, capi)
+    pk = aggregate_profile(prof, ms)
+    key = "float_float_form" if other == "df" else "fp64_native_form"
+    out[key] = {"dtype": ARITH_LABEL[other], "r_max": args.rmax, "ms": ms,
+                "gbs": in_bytes / (ms / 1e3) / 1e9, "two_read_frac": two_read_ms / ms,
+                "roofline": roofline_of(pk[0], other, alu_peaks, hbm_peak, peak_src,
+                                        f"{args.n}^{args.d} f64 r_max={args.rmax} {other}"),
+                "per_kernel": pk[:6], "ranks": p.result().ranks}
+    del p
+    # r_max sweep in both arithmetics (outside the timed region)
+    for ar, reps in ((args.arith, 2), (other, 2)):
+        sweep = {}
+        for r in (1, 5, 10, 20, 50):
+            p = api.TTSVDPlan(dims, r, 0.0, torch.float64, ar)
+            ms, _ = time_plan(torch, p, X, reps if ar == "df" or r < 50 else 1, stream)
+            sweep[str(r)] = {"ms": ms, "gbs": in_bytes / (ms / 1e3) / 1e9, "two_read_frac": two_read_ms / ms}
+            del p
+        out[f"rmax_sweep_{ar}"] = sweep
+    out.update(bench_planted(args, api, torch, dims, nbar, in_bytes, stream, two_read_ms))
+    # thick-bounds variant (Alg. 3, m_min = 16, f1_min = 1/2) and two-sided variant (Alg. 4)
+    # beside the plain algorithm, float-float arithmetic
+    thick, two = {}, {}
     for r in (1, 5, 10):
-        p = api.TTSVDPlan(dims, r, 0.0, torch.float64, args.arith, thick=(16, 0.5))
-        p.run(X)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(2):
-            p.run(X)
-        b.record(stream)
-        torch.cuda.synchronize()
-        res = p.result()
-        thick[str(r)] = {"ms": a.elapsed_time(b) / 2, "ranks": res.ranks}
+        p = api.TTSVDPlan(dims, r, 0.0, torch.float64, "df", thick=(16, 0.5))
+        ms, _ = time_plan(torch, p, X, 2, stream)
+        thick[str(r)] = {"ms": ms, "ranks": p.result().ranks}
         del p
-    out["thick_bounds_fp64"] = thick
-    # two-sided variant (Alg. 4)
-    two = {}
     for r in (5, 10):
-        p = api.TTSVDPlan(dims, r, 0.0, torch.float64, args.arith, two_sided=True)
-        p.run(X)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(2):
-            p.run(X)
-        b.record(stream)
-        torch.cuda.synchronize()
-        res = p.result()
-        two[str(r)] = {"ms": a.elapsed_time(b) / 2, "ranks": res.ranks}
+        p = api.TTSVDPlan(dims, r, 0.0, torch.float64, "df", two_sided=True)
+        ms, _ = time_plan(torch, p, X, 2, stream)
+        two[str(r)] = {"ms": ms, "ranks": p.result().ranks}
         del p
-    out["two_sided_fp64"] = two
-    # r_max sweep (outside the timed region)
-    sweep = {}
-    for r in (1, 5, 10, 20, 50):
-        p = api.TTSVDPlan(dims, r, 0.0, torch.float64, args.arith)
-        p.run(X)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 2
-        a.record(stream)
-        for _ in range(reps):
-            p.run(X)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / reps
-        sweep[str(r)] = {"ms": ms, "gbs": in_bytes / (ms / 1e3) / 1e9,
-                         "two_read_frac": (2 * in_bytes / (hbm_peak * 1e9) * 1e3) / ms}
-        del p
-    out["rmax_sweep_fp64"] = sweep
-    # FP32-storage form, r_max = 32, and its error against the FP64 form
-    X32 = api.gen_uniform(nbar, args.seed, torch.float32)
-    p32 = api.TTSVDPlan(dims, 32, 0.0, torch.float32, "df")
-    p64 = api.TTSVDPlan(dims, 32, 0.0, torch.float64, args.arith)
-    p32.run(X32)
-    r32 = p32.result()
-    p64.run(X)
-    r64 = p64.result()
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 3
-    a.record(stream)
-    for _ in range(reps):
-        p32.run(X32)
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms32 = a.elapsed_time(b) / reps
-    a.record(stream)
-    for _ in range(reps):
-        p64.run(X)
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms64 = a.elapsed_time(b) / reps
-    nx = math.sqrt(float((X * X).sum().item()))
-    out["fp32_form"] = {"r_max": 32, "ms": ms32, "gbs_fp32_input": nbar * 4 / (ms32 / 1e3) / 1e9,
-                        "entries_per_s": nbar / (ms32 / 1e3), "fp64_form_ms_same_rmax": ms64,
-                        "speedup_vs_fp64_form": ms64 / ms32,
-                        "rel_err_fp32": math.sqrt(max(r32.err2, 0.0)) / nx,
-                        "rel_err_fp64": math.sqrt(max(r64.err2, 0.0)) / nx,
-                        "rel_err_diff": abs(math.sqrt(max(r32.err2, 0.0)) - math.sqrt(max(r64.err2, 0.0))) / nx}
-    del X32, p32, p64
+    out["thick_bounds_df"] = thick
+    out["two_sided_df"] = two
+    out["fp32_form"] = bench_fp32_form(args, api, torch, X, dims, nbar, stream, hbm_peak)
     out["batched"] = bench_batched(api, capi, torch, stream, args.seed)
     out["serve"] = bench_serve(api, capi, torch, args.seed, args.serve_seconds)
     # oracle on the host cores
     gbs, sec, cores, sample = cpu_oracle_rate(args.n, args.rmax, args.cpu_seconds, args.seed)
     out["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
                            "sample": sample, "seconds_per_sample": sec}
+    return out
+
+
+def bench_planted(args, api, torch, dims, nbar, in_bytes, stream, two_read_ms):
+    """The second input of the 8^10 configuration: planted TT rank 16 (Gaussian cores,
+    ||X||_F = 1) plus Gaussian noise with ||E||_F = 1e-6, built on the device; r_max in
+    {10, 20, 50}, both arithmetics."""
+    from paper_2102_00104_gb300.inputs import planted_tt_device
+    Xp = planted_tt_device(dims, 16, args.seed + 1, noise_rel=1e-6)
+    out = {"input": "planted TT rank 16 + 1e-6 relative Gaussian noise (reading c15), seed "
+                    f"{args.seed + 1}, built on the device"}
+    for ar in ("f64", "df"):
+        leg = {}
+        for r in (10, 20, 50):
+            p = api.TTSVDPlan(dims, r, 0.0, torch.float64, ar)
+            ms, _ = time_plan(torch, p, Xp, 1, stream)
+            res = p.result()
+            leg[str(r)] = {"ms": ms, "gbs": in_bytes / (ms / 1e3) / 1e9, "two_read_frac": two_read_ms / ms,
+                           "ranks": res.ranks, "rel_err": (max(res.err2, 0.0) ** 0.5)}
+            del p
+        out[ar] = leg
+    del Xp
+    return {"planted_rank16": out}
+
+
+def bench_fp32_form(args, api, torch, X, dims, nbar, stream, hbm_peak):
+    """FP32-storage form (r_max = 32) against the FP64 form at the same r_max: time, and
+    per tensor ||X~32 - X~64||_F / ||X||_F and ||X - X~||_F / ||X||_F, with X~ contracted
+    on the device (X~64 from native FP64 arithmetic)."""
+    X32 = api.gen_uniform(nbar, args.seed, torch.float32)  # the same values, rounded to FP32
+    p32 = api.TTSVDPlan(dims, 32, 0.0, torch.float32, "df")
+    ms32, _ = time_plan(torch, p32, X32, 3, stream)
+    r32 = p32.result()
+    out = {"r_max": 32, "ms": ms32, "gbs_fp32_input": nbar * 4 / (ms32 / 1e3) / 1e9,
+           "entries_per_s": nbar / (ms32 / 1e3),
+           "two_read_frac": (2 * nbar * 4 / (hbm_peak * 1e9) * 1e3) / ms32, "ranks": r32.ranks}
+    nx = float(torch.linalg.vector_norm(X).item())
+    T32 = tt_full_device(torch, r32.cores, dims)
+    del p32, X32
+    out["rel_err_vs_X"] = float(torch.linalg.vector_norm(X - T32).item()) / nx
+    for ar in ("f64", "df"):
+        p64 = api.TTSVDPlan(dims, 32, 0.0, torch.float64, ar)
+        ms64, _ = time_plan(torch, p64, X, 1, stream)
+        T64 = tt_full_device(torch, p64.result().cores, dims)
+        out[f"fp64_form_{ar}"] = {"ms": ms64, "speedup_of_fp32_form": ms64 / ms32,
+                                  "rel_err_vs_X": float(torch.linalg.vector_norm(X - T64).item()) / nx,
+                                  "rel_diff_fp32_form": float(torch.linalg.vector_norm(T32 - T64).item()) / nx}
+        del p64, T64
+    del T32
+    out["note"] = ("rel_diff_fp32_form = ||X~32 - X~64||_F / ||X||_F: the FP32 form against the FP64 "
+                   "form on the same tensor (it includes the FP32 rounding of the input)")
     return out
 
 
@@ -597,26 +665,25 @@ def bench_batched(api, capi, torch, stream, seed, count=256):
 
 
 def bench_serve(api, capi, torch, seed, seconds):
-    """Poisson arrivals (200 req/s) for a bounded time.  Requests: d 6..14, n_j from
-    {2,3,4,8}, 50/50 FP64/FP32; half use r_max in {4,8,16,32} on uniform inputs of
-    2^14..2^24 entries, half use tol in {1e-2,1e-4} (r_max cap 32) on planted-rank
-    inputs (ranks 4..32, 1e-3 relative noise) of 2^14..2^22 entries.  Inputs come from
-    a pool of device-resident tensors made before the arrivals (not timed)."""
+    """The serving configuration: Poisson arrivals at 200 req/s for `seconds`; requests with
+    d in 6..14, n_j from {2,3,4,8} and 2^14..2^28 entries (log-uniform), 50/50 FP64/FP32;
+    half use r_max in {4,8,16,32} on uniform inputs, half tol in {1e-2,1e-4} with an r_max
+    cap of 64 on planted-rank inputs (ranks 4..32, 1e-3 relative noise).  Inputs come from a
+    pool of 48 device-resident tensors made before the arrivals (not timed); the server
+    admits requests under a 150 GB budget with 16 slots."""
     import numpy as np
-    from paper_2102_00104_gb300.inputs import planted_tt
+    from paper_2102_00104_gb300.inputs import planted_tt_device
     rng = np.random.default_rng(seed + 5)
     pool = []
     for t in range(48):
         dt = torch.float64 if t % 2 == 0 else torch.float32
+        dims = draw_shape(rng, 14, 28, 6, 14)
         if t % 4 < 2:
-            dims = draw_shape(rng, 14, 24, 6, 14)
             X = api.gen_uniform(int(np.prod(dims)), seed + 20000 + t, dt)
             spec = (int(rng.choice([4, 8, 16, 32])), 0.0)
         else:
-            dims = draw_shape(rng, 14, 22, 6, 14)
-            Xh = planted_tt(dims, int(rng.integers(4, 33)), seed=t, noise_rel=1e-3)
-            X = torch.from_numpy(Xh.ravel(order="F").copy()).to("cuda", dt)
-            spec = (32, float(rng.choice([1e-2, 1e-4])))
+            X = planted_tt_device(dims, int(rng.integers(4, 33)), seed + 30000 + t, noise_rel=1e-3).to(dt)
+            spec = (64, float(rng.choice([1e-2, 1e-4])))
         pool.append((dims, X, spec))
     torch.cuda.synchronize()
     srv = capi.tt_serve_create(150 << 30, max_inflight=16, arena_bytes=48 << 30)
@@ -633,7 +700,7 @@ def bench_serve(api, capi, torch, seed, seconds):
         dims, X, (r, tol) = pool[int(pk)]
         j = api.Job(X, dims, r, tol)
         jobs.append(j)
-        tickets.append(capi.tt_serve_submit(srv, j.c))
+        tickets.append(api.serve_submit(srv, j))
         nbytes += X.numel() * X.element_size()
     lat, bad = [], 0
     first_submit, last_done = None, None
@@ -642,6 +709,7 @@ def bench_serve(api, capi, torch, seed, seconds):
         if code != capi.TT_OK or res.status != capi.TT_OK:
             bad += 1
             continue
+        capi.tt_serve_release(srv, t)
         lat.append(res.t_done - res.t_submit)
         first_submit = res.t_submit if first_submit is None else min(first_submit, res.t_submit)
         last_done = res.t_done if last_done is None else max(last_done, res.t_done)
@@ -650,10 +718,14 @@ def bench_serve(api, capi, torch, seed, seconds):
     p50 = lat[len(lat) // 2] * 1e3 if lat else None
     p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3 if lat else None
     span = (last_done - first_submit) if lat else None
+    sizes = sorted(int(np.prod(d)) for d, _, _ in pool)
     return {"requests": n_req, "seconds_of_arrivals": seconds, "rate_per_s": 200,
             "p50_ms": p50, "p99_ms": p99, "failed": bad, "input_bytes": nbytes,
             "gbs": nbytes / span / 1e9 if span else None,
-            "sizes": "r_max jobs 2^14..2^24 entries, tol jobs 2^14..2^22 (r_max cap 32), d 6..14, pool of 48 device-resident inputs",
+            "offered_gbs": nbytes / seconds / 1e9,
+            "sizes": "2^14..2^28 entries (log-uniform), d 6..14, n_j in {2,3,4,8}, 50/50 FP64/FP32; "
+                     "r_max in {4,8,16,32} or tol in {1e-2,1e-4} (r_max cap 64); pool of 48 "
+                     f"device-resident inputs, largest {sizes[-1]} entries",
             "budget_bytes": 150 << 30, "slots": 16}
 
 
