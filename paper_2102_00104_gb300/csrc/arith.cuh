@@ -317,33 +317,34 @@ __device__ __forceinline__ float flush_tiny(float a) { return a; }
 // exponents below the normal FP32 range flush to zero, above it overflow to infinity;
 // the caller picks sh so that neither happens to entries that matter (engine.h, XRange).
 __device__ __forceinline__ df df_from_f64_sh(double x, int sh) {
+  // branch-free (selects only), so that an unrolled run of loads and conversions keeps
+  // its loads together
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  int e = (int)((b >> 52) & 0x7FF);
-  unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-  if (e == 0) {
-    if (mant == 0ull) return mkdf(0.f, 0.f);
-    // subnormal: move the leading bit to the implicit position (integer operations only);
-    // the exponent field becomes 1 - s <= 0
-    const int s = __clzll((long long)mant) - 11;
-    mant = (mant << s) & 0xFFFFFFFFFFFFFull;
-    e = 1 - s;
-  }
+  const int e0 = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m0 = b & 0xFFFFFFFFFFFFFull;
+  // a subnormal moves its leading bit to the implicit position (s = 0 for normal values)
+  const int s = e0 == 0 ? __clzll((long long)m0) - 11 : 0;
+  const unsigned long long mant = (m0 << s) & 0xFFFFFFFFFFFFFull;
+  const int e = e0 == 0 ? 1 - s : e0;
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  if (e == 2047)  // infinity stays infinity, NaN stays NaN
-    return mkdf(__int_as_float((int)(sign | 0x7F800000u | (mant ? 0x400000u : 0u))), 0.f);
   const int fe = e - 1023 + 127 - sh;
-  if (fe <= 0) return mkdf(0.f, 0.f);
-  if (fe >= 255) return mkdf(__int_as_float((int)(sign | 0x7F800000u)), 0.f);
-  const float hi = __int_as_float((int)(sign | ((unsigned)fe << 23) | (unsigned)(mant >> 29)));
+  const float hi = __int_as_float((int)(sign | ((unsigned)(fe & 0xFF) << 23) | (unsigned)(mant >> 29)));
   // remaining 29 bits; keep the top 23 of them as an exact small integer
   const unsigned rem23 = (unsigned)((mant & 0x1FFFFFFFull) >> 6);
   const float f = __fsub_rn(__int_as_float((int)(0x4B000000u | rem23)), 8388608.0f);
   // value of one unit of rem23: 2^(e - 1023 - 52 + 6 - sh)
   const int se = e - 1069 + 127 - sh;
-  const float scale = se > 0 ? __int_as_float(se << 23) : 0.f;
-  float lo = __fmul_rn(f, scale);
+  const float scale = __int_as_float((se > 0 ? (se < 255 ? se : 254) : 0) << 23);
+  float lo = se > 0 ? __fmul_rn(f, scale) : 0.f;
   lo = sign ? -lo : lo;
-  return mkdf(hi, lo);
+  // infinity stays infinity, NaN stays NaN; out of range: zero or infinity
+  const float special = __int_as_float((int)(sign | 0x7F800000u | (m0 ? 0x400000u : 0u)));
+  const float inf = __int_as_float((int)(sign | 0x7F800000u));
+  const bool zero = (e0 == 0 && m0 == 0ull) || fe <= 0;
+  const bool over = fe >= 255;
+  float rh = e0 == 2047 ? special : (over ? inf : (zero ? 0.f : hi));
+  float rl = (e0 == 2047 || over || zero) ? 0.f : lo;
+  return mkdf(rh, rl);
 }
 __device__ __forceinline__ df df_from_f64_bits(double x) { return df_from_f64_sh(x, 0); }
 
@@ -410,6 +411,7 @@ struct XRead {
   int sh = 0;
   bool flush = false;
   unsigned efield = 0;
+  __device__ __forceinline__ void set(int shift, bool fl) { sh = shift; flush = fl; }
   __device__ __forceinline__ C operator()(S x) { return Ld<C, S>::f(x); }
   __device__ __forceinline__ static int seen_of(unsigned) { return 0; }
 };
@@ -418,16 +420,42 @@ struct XRead<df, double> {
   int sh = 0;
   bool flush = false;    // true once sh comes from the input's exponent range
   unsigned efield = 0;   // largest (hi word & 0x7FF00000) seen, i.e. the exponent field << 20
+  // exponent fields [lo, lo + span] convert on the fast path: normal, not below the flush
+  // threshold, and inside FP32's range after the shift
+  int lo = 897;
+  unsigned span = 1150 - 897;
+  __device__ __forceinline__ void set(int shift, bool fl) {
+    sh = shift;
+    flush = fl;
+    const int l = max(1, (fl ? 1023 - kXrFlush : 897) + shift);
+    const int h = min(2046, 1150 + shift);
+    lo = l;
+    span = h >= l ? (unsigned)(h - l) : 0u;
+    if (h < l) lo = 4096;  // nothing is fast
+  }
   __device__ __forceinline__ df operator()(double x) {
-    const unsigned h = (unsigned)__double2hiint(x) & 0x7FF00000u;
+    const unsigned hw = (unsigned)__double2hiint(x);
+    const unsigned lw = (unsigned)__double2loint(x);
+    const unsigned h = hw & 0x7FF00000u;
     efield = max(efield, h);
-    if (!flush) return df_from_f64_sh(x, sh);
+    const int e0 = (int)(h >> 20);
+    if ((unsigned)(e0 - lo) <= span) {
+      // the top 24 significant bits in hi, the next 23 in lo (as df_from_f64_sh)
+      const int fe = e0 - 896 - sh;
+      const float hi = __uint_as_float((hw & 0x80000000u) | ((unsigned)fe << 23) |
+                                       ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+      const unsigned rem23 = (lw >> 6) & 0x7FFFFFu;
+      const float f = __fsub_rn(__uint_as_float(0x4B000000u | rem23), 8388608.0f);
+      const int se = fe - 46;
+      float lof = __fmul_rn(f, __uint_as_float(se > 0 ? (unsigned)se << 23 : 0u));
+      return mkdf(hi, (hw & 0x80000000u) ? -lof : lof);
+    }
+    // zero, subnormal, below the flush threshold, too large, infinity, NaN
     // floor(log2 |x|) < sh - kXrFlush: for a normal x its exponent field is below
     // 1023 + sh - kXrFlush; a subnormal x (field 0, |x| < 2^-1022) is below whenever
     // sh - kXrFlush > -1023 (otherwise the whole tensor is of subnormal size: kept)
-    const int f = (int)(h >> 20);
-    if (f != 0 ? f < 1023 + sh - kXrFlush : sh - kXrFlush > -1023) return mkdf(0.f, 0.f);
-    return df_from_f64_sh(x, sh);
+    const bool tiny = flush && (e0 != 0 ? e0 < 1023 + sh - kXrFlush : sh - kXrFlush > -1023);
+    return tiny ? mkdf(0.f, 0.f) : df_from_f64_sh(x, sh);
   }
   // encoded exponent (engine.h, XRange) of the largest field (subnormals count as zero:
   // only large entries can leave the safe window)
@@ -439,28 +467,40 @@ struct XRead<df, double> {
 // FP32 value times 2^-sh, exactly (exponent arithmetic); with `flush`, values below
 // 2^(sh - kXrFlush) are read as zero (the same rule as for FP64 input)
 __device__ __forceinline__ float f32_shift(float x, int sh, bool flush) {
-  unsigned b = __float_as_uint(x);
-  int e = (int)((b >> 23) & 0xFF);
-  if (e == 255) return x;                 // infinity, NaN
-  if (e == 0) {
-    if ((b << 1) == 0u) return x;         // +-0
-    b = __float_as_uint(x * 16777216.0f); // subnormal: x 2^24, exact
-    e = (int)((b >> 23) & 0xFF);
-    sh += 24;
-  }
-  if (flush && e - 127 < sh - kXrFlush) return 0.f;
-  const int fe = e - sh;
-  if (fe <= 0) return 0.f;
-  if (fe >= 255) return __uint_as_float((b & 0x80000000u) | 0x7F800000u);
-  return __uint_as_float((b & 0x807FFFFFu) | ((unsigned)fe << 23));
+  // branch-free (selects only); a subnormal is first scaled by 2^24 (exact)
+  const unsigned b0 = __float_as_uint(x);
+  const int e0 = (int)((b0 >> 23) & 0xFF);
+  const bool sub = e0 == 0;
+  const unsigned b = sub ? __float_as_uint(x * 16777216.0f) : b0;
+  const int e = (int)((b >> 23) & 0xFF);
+  const int shx = sub ? sh + 24 : sh;
+  const int fe = e - shx;
+  const float v = __uint_as_float((b & 0x807FFFFFu) | ((unsigned)(fe & 0xFF) << 23));
+  const float inf = __uint_as_float((b & 0x80000000u) | 0x7F800000u);
+  const bool zero = (b0 << 1) == 0u || fe <= 0 || (flush && e - 127 < shx - kXrFlush);
+  return e0 == 255 ? x : (fe >= 255 ? inf : (zero ? 0.f : v));
 }
 template <>
 struct XRead<float, float> {
   int sh = 0;
   bool flush = false;
   unsigned efield = 0;   // largest (bits & 0x7F800000) seen, i.e. the exponent field << 23
+  int lo = 1;            // exponent fields [lo, lo + span]: shifted by subtracting sh << 23
+  unsigned span = 253;
+  __device__ __forceinline__ void set(int shift, bool fl) {
+    sh = shift;
+    flush = fl;
+    const int l = max(1, (fl ? 127 - kXrFlush : 1) + shift);
+    const int h = min(254, 254 + shift);
+    lo = l;
+    span = h >= l ? (unsigned)(h - l) : 0u;
+    if (h < l) lo = 4096;
+  }
   __device__ __forceinline__ float operator()(float x) {
-    efield = max(efield, __float_as_uint(x) & 0x7F800000u);
+    const unsigned b = __float_as_uint(x);
+    const unsigned ef = b & 0x7F800000u;
+    efield = max(efield, ef);
+    if ((unsigned)((int)(ef >> 23) - lo) <= span) return __uint_as_float(b - ((unsigned)sh << 23));
     return f32_shift(x, sh, flush);
   }
   // encoded exponent (engine.h, XRange) of the largest field (subnormals count as zero)
@@ -475,9 +515,12 @@ struct XRead<df, float> {
   int sh = 0;
   bool flush = false;
   unsigned efield = 0;
+  __device__ __forceinline__ void set(int shift, bool fl) {
+    sh = shift;
+    flush = fl;
+    r.set(shift, fl);
+  }
   __device__ __forceinline__ df operator()(float x) {
-    r.sh = sh;
-    r.flush = flush;
     const float v = r(x);
     efield = r.efield;
     return mkdf(v, 0.f);
@@ -490,8 +533,7 @@ template <class C, class S>
 __device__ __forceinline__ bool xr_begin(const XRange* xr, int xfix, XRead<C, S>& rd) {
   if (!xr) return true;
   if (xfix && !xr->redo) return false;
-  rd.sh = xfix ? xr->k : tt::xr_shift_for(xr->sample);
-  rd.flush = true;
+  rd.set(xfix ? xr->k : tt::xr_shift_for(xr->sample), true);
   return true;
 }
 // End of such a kernel: the largest exponent of the first pass, one atomic per warp.

@@ -24,8 +24,7 @@ k_tsmm(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict_
        int* status, const XRange* xr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   XRead<C, S> rd;
-  rd.sh = xr ? xr->k : 0;
-  rd.flush = xr != nullptr;
+  rd.set(xr ? xr->k : 0, xr != nullptr);
   const int m = m_ptr ? *m_ptr : m_val;
   const int r = r_ptr ? *r_ptr : r_val;
   if (m < 1 || m > m_max || r < 1 || r > r_max || r > m || rc < 1) {
@@ -83,8 +82,7 @@ k_tsmm_rb(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
           const XRange* xr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   XRead<C, S> rd;
-  rd.sh = xr ? xr->k : 0;
-  rd.flush = xr != nullptr;
+  rd.set(xr ? xr->k : 0, xr != nullptr);
   const int m = m_ptr ? *m_ptr : m_val;
   const int r = r_ptr ? *r_ptr : r_val;
   if (m < 1 || m > m_max || r < 1 || r > r_max || r > m) {

@@ -61,8 +61,7 @@ k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
           const XRange* xr) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   XRead<df, S> rd;  // W read as W 2^-sh (FP64 input of the float-float form)
-  rd.sh = xr ? xr->k : 0;
-  rd.flush = xr != nullptr;
+  rd.set(xr ? xr->k : 0, xr != nullptr);
   const int m = m_ptr ? *m_ptr : m_val;
   const int r = r_ptr ? *r_ptr : r_val;
   if (m < 1 || m > m_max || m_max > OZ_MAXM || r < 1 || r > r_max || r > m || r > 8 * NT ||

@@ -212,8 +212,7 @@ k_tsmm_tc(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
     __syncthreads();
     key = max(max(s_key[0][i], s_key[1][i]), max(s_key[2][i], s_key[3][i]));
     XRead<df, S> rd;  // W read as W 2^-sh (FP64 input of the float-float form)
-    rd.sh = xr ? xr->k : 0;
-    rd.flush = xr != nullptr;
+    rd.set(xr ? xr->k : 0, xr != nullptr);
     const int be = oz_bexp_of(key, (S*)nullptr, rd.sh);
     if (q == 0) Erow[i] = be;
     const float sc = oz_inv_scale(be);

@@ -69,12 +69,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// wait for the completion of the phase with the given parity; false once kWaitCycles passed
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+// wait for the completion of the phase with the given parity; false once `limit` SM clock
+// cycles passed (kWaitCycles, about 2 s, in the kernels)
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, long long limit = kWaitCycles) {
   if (mbar_test(b, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_test(b, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 
@@ -325,13 +326,26 @@ k_tsqr_col(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restr
   uint32_t g = 0;  // running pivot number of this CTA (m per panel)
   for (int64_t p = p0; p < p1; ++p, g += (uint32_t)m) {
     C a[CLW][PRL];
+    {
+      // every load of the panel first, then the conversions (which may branch)
+      S raw[CLW][PRL];
 #pragma unroll
-    for (int c = 0; c < CLW; ++c) {
-      const int k = w + NW * c;
+      for (int c = 0; c < CLW; ++c) {
+        const int k = w + NW * c;
 #pragma unroll
-      for (int q = 0; q < PRL; ++q) {
-        const int64_t row = p * PR + lane + 32 * q;
-        a[c][q] = (row < rows && k < m) ? rd(W[row + (int64_t)k * ld]) : Tr<C>::zero();
+        for (int q = 0; q < PRL; ++q) {
+          const int64_t row = p * PR + lane + 32 * q;
+          raw[c][q] = (row < rows && k < m) ? W[row + (int64_t)k * ld] : S{};
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CLW; ++c) {
+        const int k = w + NW * c;
+#pragma unroll
+        for (int q = 0; q < PRL; ++q) {
+          const int64_t row = p * PR + lane + 32 * q;
+          a[c][q] = (row < rows && k < m) ? rd(raw[c][q]) : Tr<C>::zero();
+        }
       }
     }
     // warm L2 with the next panel of this CTA (two requests per 256-byte column segment)

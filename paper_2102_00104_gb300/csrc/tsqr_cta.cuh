@@ -62,14 +62,26 @@ k_tsqr_cta(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restr
   const int64_t p1 = (int64_t)(blockIdx.x + 1) * npanels / gridDim.x;
   for (int64_t p = p0; p < p1; ++p) {
     C a[RL][CL];
+    {
+      // every load of the panel first, then the conversions (which may branch)
+      S raw[RL][CL];
 #pragma unroll
-    for (int q = 0; q < RL; ++q) {
-      const int64_t row = p * PR + rg + RG * q;
-      const bool ok = row < rows;
+      for (int q = 0; q < RL; ++q) {
+        const int64_t row = p * PR + rg + RG * q;
 #pragma unroll
-      for (int c = 0; c < CL; ++c) {
-        const int k = cg + CG * c;
-        a[q][c] = (ok && k < m) ? rd(W[row + (int64_t)k * ld]) : Tr<C>::zero();
+        for (int c = 0; c < CL; ++c) {
+          const int k = cg + CG * c;
+          raw[q][c] = (row < rows && k < m) ? W[row + (int64_t)k * ld] : S{};
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RL; ++q) {
+        const int64_t row = p * PR + rg + RG * q;
+#pragma unroll
+        for (int c = 0; c < CL; ++c) {
+          const int k = cg + CG * c;
+          a[q][c] = (row < rows && k < m) ? rd(raw[q][c]) : Tr<C>::zero();
+        }
       }
     }
     for (int j = 0; j < m; ++j) {

@@ -13,43 +13,44 @@
 
 namespace tt {
 
-template <int MAXM, int K, int NW, class C, class S, class RO>
-__global__ void __launch_bounds__(NW * 32)
-k_tsqr_narrow(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
-              int m_val, RO* __restrict__ Rout, int64_t ldR, int mb, int64_t npanels, int* status,
-              int normalize, XRange* xr, int xfix) {
+// Rows of the panel from a column-major matrix W (rows x m, leading dimension ld), read
+// through the input reader (exponent shift of X, see arith.cuh).
+template <class C, class S>
+struct MatRows {
+  const S* W;
+  int64_t ld;
+  XRead<C, S> rd;
+  template <int MAXM>
+  __device__ __forceinline__ void row(int64_t r, bool ok, int m, C (&out)[MAXM]) {
+    // every load of the row first, then the conversions (which may branch)
+    S raw[MAXM];
+#pragma unroll
+    for (int k = 0; k < MAXM; ++k) raw[k] = (ok && k < m) ? W[r + (int64_t)k * ld] : S{};
+#pragma unroll
+    for (int k = 0; k < MAXM; ++k) out[k] = (ok && k < m) ? rd(raw[k]) : Tr<C>::zero();
+  }
+};
+
+// The narrow TSQR of one warp's panels (flat tree): rows come from `src.row`.
+template <int MAXM, int K, class C, class RO, class Src>
+__device__ __forceinline__ void narrow_body(Src& src, C (*R)[MAXM], int64_t rows, int m,
+                                            RO* __restrict__ Rout, int64_t ldR, int mb,
+                                            int64_t p0, int64_t p1, int64_t gw, int normalize) {
   constexpr int PR = 32 * K;
   constexpr int LG = MAXM == 4 ? 2 : (MAXM == 8 ? 3 : 4);  // log2(MAXM)
   constexpr int G = 32 / MAXM;                               // lanes per column after the butterfly
   static_assert((1 << LG) == MAXM, "MAXM is 4, 8 or 16");
-  __shared__ C Rsh[NW][MAXM][MAXM];
-  XRead<C, S> rd;
-  if (!xr_begin(xr, xfix, rd)) return;
-  const int m = m_ptr ? *m_ptr : m_val;
-  const int nwb = blockDim.x >> 5;
-  if (m < 1 || m > MAXM || m > mb || nwb > NW) {
-    if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
-    return;
-  }
   const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * nwb + w;
-  const int64_t nwt = (int64_t)gridDim.x * nwb;
-  C(*R)[MAXM] = Rsh[w];
   for (int i = lane; i < MAXM * MAXM; i += 32) R[i / MAXM][i % MAXM] = Tr<C>::zero();
   __syncwarp();
   const C eps = Tr<C>::eps();
-  const int64_t p0 = gw * npanels / nwt, p1 = (gw + 1) * npanels / nwt;
   for (int64_t p = p0; p < p1; ++p) {
     C a[K][MAXM];
     const int64_t r0 = p * PR;
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const int64_t row = r0 + lane + 32 * q;
-      const bool ok = row < rows;
-#pragma unroll
-      for (int k = 0; k < MAXM; ++k)
-        a[q][k] = (ok && k < m) ? rd(W[row + (int64_t)k * ld]) : Tr<C>::zero();
+      src.template row<MAXM>(row, row < rows, m, a[q]);
     }
     for (int j = 0; j < m; ++j) {
       // pivot column j, renormalised (a product of two float-float pairs drops lo*lo)
@@ -122,7 +123,6 @@ k_tsqr_narrow(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __re
       __syncwarp();
     }
   }
-  xr_end(xr, xfix, rd);
   // stacked output block: rows gw*mb + i (i < mb), columns k < m
   for (int idx = lane; idx < mb * m; idx += 32) {
     const int i = idx % mb, k = idx / mb;
@@ -130,6 +130,28 @@ k_tsqr_narrow(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __re
     if (i < MAXM && i <= k) v = R[i][k];
     Rout[gw * mb + i + (int64_t)k * ldR] = st_as<RO>(v);
   }
+}
+
+template <int MAXM, int K, int NW, class C, class S, class RO>
+__global__ void __launch_bounds__(NW * 32)
+k_tsqr_narrow(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
+              int m_val, RO* __restrict__ Rout, int64_t ldR, int mb, int64_t npanels, int* status,
+              int normalize, XRange* xr, int xfix) {
+  __shared__ C Rsh[NW][MAXM][MAXM];
+  MatRows<C, S> src{W, ld, {}};
+  if (!xr_begin(xr, xfix, src.rd)) return;
+  const int m = m_ptr ? *m_ptr : m_val;
+  const int nwb = blockDim.x >> 5;
+  if (m < 1 || m > MAXM || m > mb || nwb > NW) {
+    if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
+    return;
+  }
+  const int w = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * nwb + w;
+  const int64_t nwt = (int64_t)gridDim.x * nwb;
+  narrow_body<MAXM, K>(src, Rsh[w], rows, m, Rout, ldR, mb, gw * npanels / nwt,
+                       (gw + 1) * npanels / nwt, gw, normalize);
+  xr_end(xr, xfix, src.rd);
 }
 
 }  // namespace tt
