@@ -60,14 +60,19 @@ def parse():
     p.add_argument("--arith", default="f64", choices=["df", "f64"],
                    help="arithmetic of the headline (f64: native FP64; df: float-float)")
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--alg5", action="store_true",
+                   help="distributed TSQR TT-SVD (Alg. 5) instead of independent problems: the "
+                        "tensor (N, n^d) is split along its first dimension over the N ranks, "
+                        "one all-gather of the partial R's per step")
     p.add_argument("--no-extras", action="store_true", help="skip sweep, FP32 form, e2e, CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--serve-seconds", type=float, default=4.0)
     p.add_argument("--case", default="", help="one building block for profiling instead of the bench: "
                    "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix), "
                    "tsmm:ROWS:M:K (W V(:, 0:K) of a uniform FP64 W) or svd:M (small SVD of a "
-                   "uniform upper-triangular R), each optionally followed by :KEY=VALUE tuning "
-                   "keys; prints one JSON line")
+                   "uniform upper-triangular R) or ttsvd:N:D:RMAX:ARITH (a whole TT-SVD of a "
+                   "uniform N^D FP64 tensor, ARITH f64 or df), each optionally followed by "
+                   ":KEY=VALUE tuning keys; prints one JSON line")
     return p.parse_args()
 
 
@@ -267,6 +272,12 @@ def run_case(spec: str) -> int:
         Y = torch.empty(rows * k, dtype=torch.float64, device="cuda")
         call = lambda: capi.tt_tsmm(W.data_ptr(), capi.TT_F64, rows, m, rows, V.data_ptr(), k,
                                     Y.data_ptr(), rows, int(s.cuda_stream))
+    elif parts[0] == "ttsvd":
+        # ttsvd:N:D:RMAX:ARITH -- a whole TT-SVD of a uniform N^D FP64 tensor
+        n, d, r, ar = int(parts[1]), int(parts[2]), int(parts[3]), parts[4]
+        X = api.gen_uniform(n ** d, 3, torch.float64)
+        plan = api.TTSVDPlan([n] * d, r, 0.0, torch.float64, ar)
+        call = lambda: plan.run(X)
     elif parts[0] == "svd":
         m = int(parts[1])
         g = torch.Generator(device="cuda").manual_seed(0)
@@ -283,6 +294,66 @@ def run_case(spec: str) -> int:
     b.record(s)
     torch.cuda.synchronize()
     print(json.dumps({"case": spec, "ms": a.elapsed_time(b) / 3}), flush=True)
+    return 0
+
+
+def run_alg5(args):
+    """Alg. 5 over the ranks of a torchrun launch: rank j holds the n^d part X[j, :, ..., :]
+    of a (world, n, ..., n) tensor (its own Philox stream, generated on its GPU); every
+    step's local TSQR, small SVD and W V_r run in the library's kernels and the partial R's
+    are all-gathered over NCCL.  value = world * (part bytes) / (max over ranks of the time
+    per decomposition)."""
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as G
+    from paper_2102_00104_gb300 import api, capi
+    from paper_2102_00104_gb300.distributed import DeviceOps, max_over_ranks, tt_svd_alg5
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        G.build()
+    if world > 1:
+        dist.barrier()
+    capi.lib()
+    K, W = max(1, args.steps), max(3, args.warmup)
+    dims = [world] + [args.n] * args.d
+    nloc = args.n ** args.d
+    part = api.gen_uniform(nloc, args.seed + 1000 * rank, torch.float64)
+    ops = DeviceOps()
+    for _ in range(W):
+        cores, ranks, _ = tt_svd_alg5([part], dims, 1, args.rmax, ops)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches0 = capi.tt_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        cores, ranks, _ = tt_svd_alg5([part], dims, 1, args.rmax, ops)
+    e1.record()
+    torch.cuda.synchronize()
+    launches = (capi.tt_stats() - launches0) // K
+    ms = max_over_ranks(e0.elapsed_time(e1) / K, device="cuda")
+    value = world * nloc * 8 / (ms / 1e3) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": ARITH_LABEL["df"], "data": "synthetic: i.i.d. uniform[0,1) from Philox4x32-10, per rank",
+            "config": {"workload": f"Alg. 5: TT-SVD of a ({world}, {args.n}^{args.d}) FP64 tensor split "
+                                   f"along its first dimension, r_max={args.rmax}, tol=0",
+                       "ranks": ranks, "parallelism": f"alg5 over {world} GPU(s): all-gather of R per step",
+                       "l2_flush": "input > L2, no flush"},
+            "gpu_launches": int(launches)}), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 
@@ -354,6 +425,8 @@ def main():
         return run_reference(args)
     if args.case:
         return run_case(args.case)
+    if args.alg5:
+        return run_alg5(args)
 
     import torch
     import torch.distributed as dist

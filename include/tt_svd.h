@@ -299,7 +299,8 @@ tt_status tt_serve_destroy(tt_server* s);
  * synchronises the recorded events and returns up to `max` records:
  * kinds[k] (0 TSQR first level, 1 TSQR upper levels, 2 SVD of R, 3 rank choice
  * and core, 4 W*V_r, 5 the exponent-range decision and the re-run of the first level
- * that it may ask for), steps[k] (the step index i), ms[k], bytes[k], flops[k],
+ * that it may ask for, 6 W*V_r of step i fused with the first TSQR level of step i-1),
+ * steps[k] (the step index i), ms[k], bytes[k], flops[k],
  * info[k] (Jacobi sweeps for kind 2 -- valid while the workspace of that call is
  * untouched -- else -1).  *n receives the number of records available.  Any
  * output array may be NULL. */
@@ -308,11 +309,20 @@ tt_status tt_profile_read(int max, int* n, int* kinds, int* steps, double* ms, d
                           double* flops, int* info);
 
 /* Arithmetic peak of this GPU, measured: kind 0 = FP32 FMA, 1 = FP64 FMA, 2 = the lazy
- * float-float multiply-add of the float-float dot products (one FP64-equivalent FMA).
+ * float-float multiply-add of the float-float dot products (one FP64-equivalent FMA),
+ * 3 = the FP64 tensor-core MMA (mma.sync m8n8k4, f64).
  * *flops_per_s = 2 x multiply-adds per second over every SM (8 CTAs of 256 threads per
  * SM, 8 independent chains per thread, a warm-up run, then one timed run of ~10 ms with
  * CUDA events on `stream`).  Synchronises `stream`.  TT_EINVAL for another kind. */
 tt_status tt_fma_rate(int kind, double* flops_per_s, void* stream);
+
+/* Self-test of the bounded device waits (failure detection without a fault): launches one
+ * CTA that waits, with the wait helper of the column-owned TSQR kernels, on an mbarrier
+ * that nothing arrives at; after limit_cycles SM clock cycles (1000 .. 4e9) the wait gives
+ * up and the kernel records DEV_ERR_TIMEOUT in the status word at the start of `work`
+ * (device, 256-byte aligned, >= 256 bytes), which tt_last_device_status(work, stream)
+ * then reports as TT_ETIMEOUT.  The context stays usable.  Asynchronous on `stream`. */
+tt_status tt_wait_selftest(void* work, int64_t limit_cycles, void* stream);
 
 /* Number of kernels this library has launched since it was loaded. */
 tt_status tt_stats(int64_t* launches);
@@ -326,6 +336,7 @@ tt_status tt_stats(int64_t* launches);
  *     "tsqr.col" [1]          column-owned first-level kernel for 16 < m <= 160; 0: row-group kernel
  *     "tsqr.col.<b>" [1]      the same per m bucket b (0: m <= 32, 1: <= 64, 2: <= 80,
  *                             3: <= 128, 4: <= 160), float-float form
+ *     "tsqr.colcfg64.<b>" [-] the same for the native FP64 arithmetic
  *     "tsqr.colcfg.<b>" [-]   column-owned layout 0..9 (warps, columns per warp, rows per
  *                             lane) for bucket b; ignored when it cannot hold m
  *     "tsqr.cols" [1]         shared-memory panel kernel for 160 < m <= 512; 0: row-group kernel
@@ -346,6 +357,10 @@ tt_status tt_stats(int64_t* launches);
  *                             ALU-bound (m >= 16 and m r >= 6 (m + r)), 2 wherever it applies
  *     "tsmm.oz_nbuf" [1]      tile buffers per CTA of that kernel (1 or 2)
  *     "tsmm.tc" [0]           1: the tcgen05 form of the same product where it applies
+ *   fusion (Alg. 2 lines 11 and 5)
+ *     "fuse.tsmm_tsqr" [0]    1: W V_r of step i computes the next unfolding inside the first
+ *                             TSQR level of step i-1 when that level is narrow (m_{i-1} <= 8,
+ *                             m_i <= 8); 0: separate launches (measured faster)
  *   batched form
  *     "batched.streams" [64]  streams of tt_svd_batched (1..128) */
 tt_status tt_tune_set(const char* key, int value);

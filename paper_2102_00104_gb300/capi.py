@@ -26,7 +26,8 @@ EXPORTED = ["tt_query", "tt_core_caps", "tt_svd", "tt_svd_ex", "tt_last_device_s
             "tt_gen_uniform", "tt_batched_query", "tt_svd_batched", "tt_serve_create",
             "tt_serve_submit", "tt_serve_poll", "tt_serve_release", "tt_serve_destroy", "tt_status_str",
             "tt_profile", "tt_profile_read", "tt_stats", "tt_last_error", "tt_small_svd_noalloc", "tt_tune_set",
-            "tt_query_from_host", "tt_svd_from_host", "tt_query_ex", "tt_range_rule", "tt_fma_rate"]
+            "tt_query_from_host", "tt_svd_from_host", "tt_query_ex", "tt_range_rule", "tt_fma_rate",
+            "tt_wait_selftest"]
 
 
 class tt_opts(C.Structure):
@@ -101,6 +102,7 @@ _SIGS = {
     "tt_tune_set": (C.c_int, [C.c_char_p, C.c_int]),
     "tt_range_rule": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tt_fma_rate": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
+    "tt_wait_selftest": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
 }
 
 
@@ -231,7 +233,7 @@ def tt_status_str(code):
 
 
 PROFILE_KINDS = {0: "tsqr_first_level", 1: "tsqr_upper_levels", 2: "svd_of_R", 3: "rank_and_core", 4: "tsmm",
-                 5: "input_range"}
+                 5: "input_range", 6: "tsmm_fused_tsqr_first_level"}
 
 
 def tt_profile(enable: bool):
@@ -303,7 +305,7 @@ def tt_serve_destroy(srv):
 
 
 TT_RANGE_NONE = -100000
-FMA_FP32, FMA_FP64, FMA_DF = 0, 1, 2
+FMA_FP32, FMA_FP64, FMA_DF, MMA_FP64 = 0, 1, 2, 3
 
 
 def tt_fma_rate(kind, stream=0) -> float:

@@ -702,7 +702,10 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
   int64_t rows = 1;
   for (int a = 0; a < d - 1; ++a) rows *= P.n[a];
   const double tol2 = (d > 1) ? P.tol * P.tol / (double)(d - 1) : 0.0;
-  for (const StepPlan& S : P.steps) {
+  bool first_level_done = false;  // the previous step's fused W V_r wrote this step's level 0
+  for (size_t si = 0; si < P.steps.size(); ++si) {
+    const StepPlan& S = P.steps[si];
+    const StepPlan* next = si + 1 < P.steps.size() ? &P.steps[si + 1] : nullptr;
     const int i = S.i;
     double* sig_step = sigma_out ? sigma_out + (int64_t)(d - i) * sig_stride : nullptr;
     if (S.elide) {
@@ -766,7 +769,9 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
           ++g_launches;
           return TT_OK;
         };
-        {
+        if (l == 0 && first_level_done) {
+          // written by the previous step's fused W V_r (tsqr_fused.cu)
+        } else {
           prof::Scope ps(l == 0 ? 0 : 1, i, (double)L.rows * mm * fmt_bytes(L.in),
                          2.0 * (double)L.rows * mm * mm, s);
           if (xr && first_active && l == 0) L.xr = xr;  // this level reads X
@@ -803,9 +808,24 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
       TT_CK(launch_core(P.comp_svd, Vout, P.ldA, st, i, cores_out[i - 1], s));
       g_launches += 2;
     }
-    // W^(i-1) = W^(i) V_r
+    // W^(i-1) = W^(i) V_r, fused with the first TSQR level of step i-1 when that is narrow
     void* Y = wb + P.off_W[S.out_buf];
-    {
+    const bool fuse = next && !next->elide && !next->wide && !next->levels.empty() &&
+                      tsmm_tsqr_fusable(next->levels[0], cur_fmt, P.comp_tsmm, P.comp_svd, P.inter,
+                                        S.m_max, S.r_max_out);
+    first_level_done = false;
+    if (fuse) {
+      const TsqrLevel& L0 = next->levels[0];
+      const double rr = (double)S.r_max_out, mn = (double)next->m_max;
+      prof::Scope ps(6, i, (double)rows * (mm * fmt_bytes(cur_fmt) + rr * fmt_bytes(P.inter)),
+                     2.0 * (double)rows * mm * rr + 2.0 * (double)L0.rows * mn * mn, s);
+      TT_CK(launch_tsmm_tsqr(L0, cur_fmt, P.comp_svd, cur, rows, &st->m[i], S.m_max, Vout, P.ldA,
+                             (int)P.n[i - 2], &st->m[i - 1], &st->r[i - 1], S.r_max_out, Y,
+                             wb + P.off_R[0], L0.warps * L0.mb, status,
+                             (xr && first_active) ? xr : nullptr, s));
+      ++g_launches;
+      first_level_done = true;
+    } else {
       const double rr = (double)S.r_max_out;
       prof::Scope ps(4, i, (double)rows * (mm * fmt_bytes(S.in_fmt) + rr * fmt_bytes(P.inter)),
                      2.0 * (double)rows * mm * rr, s);
@@ -1284,10 +1304,12 @@ tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, d
     TsqrLevel L = lv[l];
     if (l == 0) L.xr = xr;
     TT_CK(launch_tsqr_level(L, lin, lld, nullptr, Rout, ldR, scr, status, s));
+    ++g_launches;
     if (L.xr) {
       TT_CK(launch_range_decide(xr, s));
       L.xfix = 1;
       TT_CK(launch_tsqr_level(L, lin, lld, nullptr, Rout, ldR, scr, status, s));
+      g_launches += 2;
     }
     lin = Rout;
     lld = ldR;
@@ -1296,6 +1318,7 @@ tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, d
     rf = lv[l].out;
   }
   // R of W = 2^k times the R of the shifted W
+  g_launches += 2;  // the sample and the copy
   return cuda_err(launch_copy_mat_f64(rf, Rfin, ldRfin, m, m, 1, R_out, m, s, xr));
 }
 
@@ -1325,6 +1348,7 @@ tt_status tt_small_svd(const double* R, int m, double* sigma, double* V, void* w
   char* Vout = A + align256(szJ);
   TT_CK(launch_jacobi(Fmt::DF, Fmt::F64, R, m, nullptr, m, A, Vw, mp, sigma, Vout, mp, status,
                       nullptr, s));
+  g_launches += 2;
   return cuda_err(launch_copy_mat_f64(Fmt::DF, Vout, mp, m, m, 0, V, m, s));
 }
 
@@ -1336,6 +1360,7 @@ tt_status tt_tsmm(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, c
   const Fmt in = dt == TT_F32 ? Fmt::F32 : Fmt::F64;
   const Fmt comp = dt == TT_F32 ? Fmt::F32 : Fmt::DF;
   TsmmCfg c = plan_tsmm(in, comp, Fmt::F64, Fmt::F64, m, k, rows, num_sms());
+  ++g_launches;
   return cuda_err(launch_tsmm(c, W, rows, ld, nullptr, V, m, nullptr, Y, ldy, nullptr,
                               (cudaStream_t)stream));
 }

@@ -233,6 +233,20 @@ cudaError_t launch_tsmm(const TsmmCfg& c, const void* W, int64_t rows, int64_t l
                         const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
                         int64_t ldy, int* status, cudaStream_t s);
 
+// ---- W V_r fused with the next step's first (narrow) TSQR level (tsqr_fused.cu) ----------
+constexpr int kFusedMaxMi = 8;     // widest W^(i) (its m) of the fused product
+// can step i's product feed the first level `next` of step i-1 directly?  (formats: in =
+// W^(i), comp = arithmetic, vfmt = V, inter = W^(i-1))
+bool tsmm_tsqr_fusable(const TsqrLevel& next, Fmt in, Fmt comp, Fmt vfmt, Fmt inter, int mi_max,
+                       int r_max);
+// Y = W^(i) V_r (rows_i = next.rows * n rows, leading dimension ldw, also of Y) and the partial
+// R's of the next step's first level (as launch_tsqr_level would write them); mi = m_i,
+// m = m_{i-1} = n r and r = r_{i-1} are device values.
+cudaError_t launch_tsmm_tsqr(const TsqrLevel& next, Fmt in, Fmt vfmt, const void* W, int64_t ldw,
+                             const int* mi_dev, int mi_max, const void* V, int ldV, int n,
+                             const int* m_dev, const int* r_dev, int r_max, void* Y, void* Rout,
+                             int64_t ldR, int* status, const XRange* xr, cudaStream_t s);
+
 // ---- generator -------------------------------------------------------------------
 cudaError_t launch_gen_uniform(void* out, Fmt f, int64_t count, uint64_t seed, int64_t start,
                                cudaStream_t s);

@@ -47,17 +47,36 @@ __global__ void __launch_bounds__(256) k_df_rate(int iters, df a, float* out) {
   if (s == -1.f) out[0] = s;
 }
 
+// FP64 tensor-core MMA (mma.sync m8n8k4, f64 in and out): NCH independent accumulator
+// tiles per warp; one MMA is 8 x 8 x 4 multiply-adds
+__global__ void __launch_bounds__(256) k_dmma_rate(int iters, double a0, double* out) {
+  double acc[NCH][2];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) { acc[c][0] = 0.0; acc[c][1] = 0.0; }
+  const double a = a0 + threadIdx.x * 1e-9, b = 1e-3;
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                   : "+d"(acc[c][0]), "+d"(acc[c][1])
+                   : "d"(a), "d"(b));
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) s += acc[c][0] + acc[c][1];
+  if (s == -1.0) out[0] = s;
+}
+
 }  // namespace
 }  // namespace tt
 
 using namespace tt;
 
 extern "C" tt_status tt_fma_rate(int kind, double* flops_per_s, void* stream) {
-  if (!flops_per_s || kind < 0 || kind > 2) return TT_EINVAL;
+  if (!flops_per_s || kind < 0 || kind > 3) return TT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const unsigned grid = (unsigned)num_sms() * 8;
   // enough steps for ~50-100 ms of work at the expected rates
-  const int iters = kind == 1 ? 2048 : (kind == 0 ? 131072 : 16384);
+  const int iters = kind == 1 ? 2048 : (kind == 0 ? 131072 : (kind == 2 ? 16384 : 256));
   void* out = nullptr;
   cudaEvent_t a = nullptr, b = nullptr;
   tt_status st = TT_OK;
@@ -70,14 +89,18 @@ extern "C" tt_status tt_fma_rate(int kind, double* flops_per_s, void* stream) {
       cudaEventRecord(a, s);
       if (kind == 0) k_fma_rate<float><<<grid, 256, 0, s>>>(iters, 0.999f, 1e-4f, (float*)out);
       else if (kind == 1) k_fma_rate<double><<<grid, 256, 0, s>>>(iters, 0.999, 1e-4, (double*)out);
-      else k_df_rate<<<grid, 256, 0, s>>>(iters, df{0.999f, 1e-9f}, (float*)out);
+      else if (kind == 2) k_df_rate<<<grid, 256, 0, s>>>(iters, df{0.999f, 1e-9f}, (float*)out);
+      else k_dmma_rate<<<grid, 256, 0, s>>>(iters, 0.999, (double*)out);
       cudaEventRecord(b, s);
       if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
           cudaEventElapsedTime(&ms, a, b) != cudaSuccess || !(ms > 0.f))
         st = TT_ECUDA;
     }
-    if (st == TT_OK)
-      *flops_per_s = 2.0 * (double)grid * 256.0 * NCH * (double)iters / (ms * 1e-3);
+    // multiply-adds per launch: one per thread, chain and step (FMA kinds); one MMA per
+    // warp, chain and step is 8 x 8 x 4 of them (kind 3)
+    const double madds = kind == 3 ? (double)grid * 8.0 * NCH * iters * 256.0
+                                   : (double)grid * 256.0 * NCH * (double)iters;
+    if (st == TT_OK) *flops_per_s = 2.0 * madds / (ms * 1e-3);
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);

@@ -3,6 +3,7 @@
 #include <cstdio>
 
 #include "tsqr_col.cuh"
+#include "tt_svd.h"
 
 namespace tt {
 
@@ -72,6 +73,12 @@ int tsqr_col_pick(int m_max, Fmt in, Fmt comp, Fmt out, int* pr, int* nw, int* p
       snprintf(key, sizeof(key), "tsqr.colcfg.%d", id);
       const int ov = tune_get(key, -1);
       if (ov >= 0 && ov <= 9 && usable(ov, m_max)) id = ov;
+    } else if (f64 && id >= 0) {
+      // native FP64: its own layout per bucket ("tsqr.colcfg64.<bucket>")
+      char key[32];
+      snprintf(key, sizeof(key), "tsqr.colcfg64.%d", id);
+      const int ov = tune_get(key, -1);
+      if (ov >= 0 && ov <= 9 && usable(ov, m_max)) id = ov;
     }
   }
   if (id < 0) return -1;
@@ -100,3 +107,27 @@ cudaError_t launch_tsqr_col(const TsqrLevel& L, const void* W, int64_t ld, const
 }
 
 }  // namespace tt
+
+// ---- self-test of the bounded waits -----------------------------------------------------
+namespace tt {
+namespace {
+// waits on an mbarrier that nothing arrives at, with the wait helper of the column-owned
+// TSQR kernels and a short limit; the wait gives up and the kernel records DEV_ERR_TIMEOUT
+__global__ void k_wait_selftest(int* status, long long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) colk::mbar_init(&bar, 1);
+  __syncthreads();
+  if (!colk::mbar_wait(&bar, 0, limit) && threadIdx.x == 0) atomicOr(status, DEV_ERR_TIMEOUT);
+}
+}  // namespace
+}  // namespace tt
+
+extern "C" tt_status tt_wait_selftest(void* work, int64_t limit_cycles, void* stream) {
+  using namespace tt;
+  if (!work || ((uintptr_t)work & 255) || limit_cycles < 1000 || limit_cycles > kWaitCycles)
+    return TT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(work, 0, sizeof(int), s) != cudaSuccess) return TT_ECUDA;
+  k_wait_selftest<<<1, 32, 0, s>>>(static_cast<int*>(work), (long long)limit_cycles);
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ECUDA;
+}

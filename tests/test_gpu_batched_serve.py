@@ -82,6 +82,38 @@ def test_batched_parity_with_oracle():
     del work
 
 
+def test_batched_parity_with_oracle_large_jobs():
+    # jobs of 2^16..2^20 entries (the upper part of the batched configuration that the oracle
+    # still decomposes in seconds), mixed FP64/FP32, in one batch with small ones
+    specs = draw_jobs(4, seed=12, max_log2=20)
+    rng = np.random.default_rng(13)
+    for t in range(3):
+        d = int(rng.integers(6, 9))
+        dims = tuple(int(x) for x in rng.choice([2, 4, 8], size=d))
+        while np.prod(dims) < 2 ** 16:
+            dims = dims + (2,)
+        while np.prod(dims) > 2 ** 20:
+            dims = dims[:-1]
+        specs.append((dims, torch.float64 if t % 2 == 0 else torch.float32, int(rng.integers(4, 33)),
+                      uniform_tensor(dims, seed=2000 + t)))
+    jobs = [api.Job(fortran_flat(X, dt), dims, r) for dims, dt, r, X in specs]
+    work = api.svd_batched(jobs)
+    torch.cuda.synchronize()
+    assert max(int(np.prod(s[0])) for s in specs) >= 2 ** 16
+    for job, (dims, dt, r, X) in zip(jobs, specs):
+        assert int(job.status.item()) == 0
+        Xr = X if dt == torch.float64 else X.astype(np.float32).astype(np.float64)
+        ref = O.tt_svd(Xr, r)
+        res = job.result()
+        assert res.ranks == ref.ranks
+        tol = 1e-10 if dt == torch.float64 else 1e-5
+        nx = np.linalg.norm(Xr)
+        err = np.linalg.norm(O.tt_full(res.core_arrays()) - Xr) / nx
+        err_ref = np.linalg.norm(O.tt_full(ref.cores) - Xr) / nx
+        assert abs(err - err_ref) <= tol
+    del work
+
+
 def test_batched_graph_capture_replays():
     specs = draw_jobs(8, seed=3)
     jobs = [api.Job(fortran_flat(X, dt), dims, r) for dims, dt, r, X in specs]
