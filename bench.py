@@ -737,13 +737,18 @@ def bench_batched(api, capi, torch, stream, seed, count=256):
             "graph": "one CUDA graph replay per batch", "jobs_with_device_errors": bad}
 
 
+# requests on the device at once: small jobs are latency-bound chains of launches, so the
+# device fills only with many of them in flight
+SERVE_SLOTS = 64
+
+
 def bench_serve(api, capi, torch, seed, seconds):
     """The serving configuration: Poisson arrivals at 200 req/s for `seconds`; requests with
     d in 6..14, n_j from {2,3,4,8} and 2^14..2^28 entries (log-uniform), 50/50 FP64/FP32;
     half use r_max in {4,8,16,32} on uniform inputs, half tol in {1e-2,1e-4} with an r_max
     cap of 64 on planted-rank inputs (ranks 4..32, 1e-3 relative noise).  Inputs come from a
     pool of 48 device-resident tensors made before the arrivals (not timed); the server
-    admits requests under a 150 GB budget with 16 slots."""
+    admits requests under a 150 GB budget with SERVE_SLOTS slots."""
     import numpy as np
     from paper_2102_00104_gb300.inputs import planted_tt_device
     rng = np.random.default_rng(seed + 5)
@@ -759,7 +764,8 @@ def bench_serve(api, capi, torch, seed, seconds):
             spec = (64, float(rng.choice([1e-2, 1e-4])))
         pool.append((dims, X, spec))
     torch.cuda.synchronize()
-    srv = capi.tt_serve_create(150 << 30, max_inflight=16, arena_bytes=48 << 30)
+    torch.cuda.empty_cache()  # the server's arena is one allocation outside torch's cache
+    srv = capi.tt_serve_create(150 << 30, max_inflight=SERVE_SLOTS, arena_bytes=96 << 30)
     n_req = int(200 * seconds)
     gaps = rng.exponential(1.0 / 200.0, size=n_req)
     picks = rng.integers(0, len(pool), size=n_req)
@@ -799,7 +805,7 @@ def bench_serve(api, capi, torch, seed, seconds):
             "sizes": "2^14..2^28 entries (log-uniform), d 6..14, n_j in {2,3,4,8}, 50/50 FP64/FP32; "
                      "r_max in {4,8,16,32} or tol in {1e-2,1e-4} (r_max cap 64); pool of 48 "
                      f"device-resident inputs, largest {sizes[-1]} entries",
-            "budget_bytes": 150 << 30, "slots": 16}
+            "budget_bytes": 150 << 30, "slots": SERVE_SLOTS, "arena_bytes": 96 << 30}
 
 
 if __name__ == "__main__":

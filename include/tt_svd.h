@@ -213,9 +213,21 @@ tt_status tt_small_svd_noalloc(const double* R, int m, double* sigma, double* V,
  *   reshape of Alg. 2 line 11 is a view of Y).  W: rows x m (ld), storage dt;
  *   V: device m x k doubles column-major (ldv = m); Y: device rows x k doubles
  *   column-major with leading dimension ldy >= rows.  Arithmetic as the
- *   matching tt_svd form (float-float for TT_F64, FP32 for TT_F32). */
+ *   matching tt_svd form (float-float for TT_F64, FP32 for TT_F32), in FP32's
+ *   exponent range: W's row maxima and the outputs must lie within [2^-100, 2^100]
+ *   in magnitude for the stated accuracy (tt_svd scales its input into that window
+ *   first; the building block does not), smaller rows lose digits or flush to zero.
+ *   tt_tsmm_ex with TT_ARITH_F64 takes any finite FP64 input. */
 tt_status tt_tsmm(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, const double* V,
                   int k, double* Y, int64_t ldy, void* stream);
+
+/* tt_tsmm in a chosen arithmetic: TT_ARITH_F64 with an FP64 W gives the native FP64 form's
+ *   product -- for m >= 16 the FP64-accurate tensor-core splitting (seven bf16-exact digits
+ *   per value taken from the FP64 bits, 28 digit products per level set, exact level sums
+ *   combined in integers and rounded once to FP64: normwise error about 2^-53 of
+ *   sum_k |W_ik||V_kj|), else FP64 multiply-adds; any other arith is tt_tsmm. */
+tt_status tt_tsmm_ex(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, const double* V,
+                     int k, double* Y, int64_t ldy, tt_arith arith, void* stream);
 
 /* tt_gen_uniform: entries start..start+count-1 of the i.i.d. uniform[0,1)
  *   stream of `seed` (Philox4x32-10, Salmon et al. SC'11; entry e is built from

@@ -182,14 +182,20 @@ def small_svd(R: torch.Tensor, stream=None):
     return sig, V.t()
 
 
-def tsmm(W: torch.Tensor, V: torch.Tensor, k: int, stream=None) -> torch.Tensor:
+def tsmm(W: torch.Tensor, V: torch.Tensor, k: int, stream=None, arith: str = "df") -> torch.Tensor:
     """Y = W V[:, :k] for W given as a (m, rows) tensor (column-major rows x m) and V (m x m FP64).
-    Returns Y as a (k, rows) FP64 tensor (column-major rows x k)."""
+    Returns Y as a (k, rows) FP64 tensor (column-major rows x k).  arith "f64" with an FP64 W:
+    the native FP64 form's product (tt_tsmm_ex)."""
     m, rows = W.shape
     Vc = V.t().contiguous()
     Y = torch.empty(k, rows, dtype=torch.float64, device=W.device)
-    capi.tt_tsmm(W.data_ptr(), _DT[W.dtype], rows, m, W.stride(0), Vc.data_ptr(), k, Y.data_ptr(),
-                 rows, _stream_ptr(stream))
+    if arith == "f64":
+        capi.check(capi.lib().tt_tsmm_ex(W.data_ptr(), _DT[W.dtype], rows, m, W.stride(0), Vc.data_ptr(), k,
+                                         Y.data_ptr(), rows, capi.TT_ARITH_F64, _stream_ptr(stream)),
+                   "tt_tsmm_ex")
+    else:
+        capi.tt_tsmm(W.data_ptr(), _DT[W.dtype], rows, m, W.stride(0), Vc.data_ptr(), k, Y.data_ptr(),
+                     rows, _stream_ptr(stream))
     torch.cuda.synchronize()
     return Y
 

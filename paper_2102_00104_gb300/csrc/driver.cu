@@ -1352,6 +1352,19 @@ tt_status tt_small_svd(const double* R, int m, double* sigma, double* V, void* w
   return cuda_err(launch_copy_mat_f64(Fmt::DF, Vout, mp, m, m, 0, V, m, s));
 }
 
+tt_status tt_tsmm_ex(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, const double* V,
+                     int k, double* Y, int64_t ldy, tt_arith arith, void* stream) {
+  if (arith != TT_ARITH_F64 || dt != TT_F64)
+    return tt_tsmm(W, dt, rows, m, ld, V, k, Y, ldy, stream);
+  if (!W || !V || !Y || rows < 1 || m < 1 || m > kMaxM || k < 1 || k > m || ld < rows || ldy < rows)
+    return TT_EINVAL;
+  // the native FP64 form's product (FP64-accurate tensor-core splitting where m >= 16)
+  TsmmCfg c = plan_tsmm(Fmt::F64, Fmt::F64, Fmt::F64, Fmt::F64, m, k, rows, num_sms());
+  ++g_launches;
+  return cuda_err(launch_tsmm(c, W, rows, ld, nullptr, V, m, nullptr, Y, ldy, nullptr,
+                              (cudaStream_t)stream));
+}
+
 tt_status tt_tsmm(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, const double* V,
                   int k, double* Y, int64_t ldy, void* stream) {
   if (!W || !V || !Y || rows < 1 || m < 1 || m > kMaxM || k < 1 || k > m || ld < rows ||

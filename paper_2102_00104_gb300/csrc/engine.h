@@ -219,7 +219,7 @@ TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int
                   int num_sms);
 // the tensor-core form (tsmm_oz.cu): usable for these formats and sizes?
 bool tsmm_oz_ok(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max);
-size_t tsmm_oz_smem(int m_max, int r_max, int nbuf);
+size_t tsmm_oz_smem(int m_max, int r_max, int nbuf, bool x64 = false);
 cudaError_t launch_tsmm_oz(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
                            const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
                            int64_t ldy, int* status, cudaStream_t s);

@@ -105,5 +105,31 @@ __device__ __forceinline__ uint32_t oz_pack(float lo_k, float hi_k) {
 template <class S>
 __device__ __forceinline__ S oz_zero() { return S{}; }
 
+// FP64-accurate splitting (native FP64 form): seven signed digits of x relative to 2^(eM -
+// 1022), the power of two above the largest magnitude of x's row (eM = that entry's biased
+// exponent field), computed with integer operations only.  x is first made the integer
+// v = x 2^(1084 - eM) (|v| < 2^62; bits below 2^-62 of the row maximum are dropped), then
+// cut from the top into d_a at weight 2^(63 - 8a), a = 1..7, each rounded to nearest (so
+// |d_a| <= 128, exact in bf16); the remainder, below 2^-56 of the row maximum, is dropped.
+__device__ __forceinline__ float oz_small_int_to_float(int q) {
+  // |q| < 2^22: 1.5 * 2^23 + q as a float, minus 1.5 * 2^23 (integer operations only)
+  return __fsub_rn(__int_as_float(0x4B400000 + q), 12582912.0f);
+}
+__device__ __forceinline__ void oz64_digits(double x, int eM, float (&d)[7]) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const long long M = (b & 0xFFFFFFFFFFFFFll) | (e ? (1ll << 52) : 0ll);
+  const int sh = 9 - (eM - (e ? e : 1));
+  long long v = sh >= 0 ? (M << sh) : (sh > -63 ? (M >> -sh) : 0ll);
+  if (b < 0) v = -v;
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+    const int p = 55 - 8 * a;
+    const long long q = (v + (1ll << (p - 1))) >> p;
+    v -= q << p;
+    d[a] = oz_small_int_to_float((int)q);
+  }
+}
+
 }  // namespace ozk
 }  // namespace tt

@@ -249,7 +249,7 @@ TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int
     // tile buffers per CTA: two (the next tile's copy overlaps this tile) or one
     // (more CTAs per SM overlap each other's copies)
     c.rc = tune_get("tsmm.oz_nbuf", 1) == 2 ? 2 : 1;
-    c.smem = tsmm_oz_smem(m_max, r_max, c.rc);
+    c.smem = tsmm_oz_smem(m_max, r_max, c.rc, comp == Fmt::F64);
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (c.smem + 1024)));
     const int64_t ntiles = (rows + 63) / 64;
     c.ctas = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nsm * per_sm));

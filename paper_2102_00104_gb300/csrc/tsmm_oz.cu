@@ -53,7 +53,11 @@ __device__ __forceinline__ void oz_mma(float (&c)[4], const uint32_t (&a)[4], ui
 // NT n-tiles of 8 output columns (r <= 8 NT).  Shared memory: two tile buffers
 // (m_max columns of OZ_CS bytes each), V's digits in B-fragment order
 // (kt x 6 x NT x 32 uint2), the column exponents, two mbarriers.
-template <int NT, class S, class VS, class SO>
+// X64 (native FP64 form): seven digits per value from its FP64 bits (oz64_digits), levels
+// 2..8 (28 digit products per k-step and n-tile), and an integer-then-FP64 combination of
+// the exact level sums, so that Y is rounded once to FP64 from a sum accurate to ~2^-56
+// of 2^(E_i + F_j).
+template <int NT, bool X64, class S, class VS, class SO>
 __global__ void __launch_bounds__(OZ_THREADS)
 k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
           int m_val, const VS* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
@@ -69,11 +73,12 @@ k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
     if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
     return;
   }
+  constexpr int ND = X64 ? 7 : 6;  // digits per value
   const int kt = (m_max + 15) / 16;
   unsigned char* buf0 = smem_raw;
   unsigned char* buf1 = smem_raw + (size_t)m_max * OZ_CS;  // (nbuf = 2)
   uint2* Bf = reinterpret_cast<uint2*>(smem_raw + nbuf * (size_t)m_max * OZ_CS);  // [kk][b][nt][lane]
-  int* Fe = reinterpret_cast<int*>(Bf + (size_t)kt * 6 * NT * 32);             // [8 NT]
+  int* Fe = reinterpret_cast<int*>(Bf + (size_t)kt * ND * NT * 32);            // [8 NT]
   uint64_t* bar = reinterpret_cast<uint64_t*>(Fe + 8 * NT);                    // [2], 8-aligned
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int g = lane >> 2, tq = lane & 3;
@@ -88,10 +93,16 @@ k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // column exponents of V(:, 0:r): F_j with |V_kj| < 2^(F_j) as a biased FP32 exponent
+  // (X64: the largest biased FP64 exponent field of the column)
   for (int j = w; j < 8 * NT; j += OZ_WARPS) {
     int be = 0;
     if (j < r)
-      for (int k = lane; k < m; k += 32) be = max(be, oz_bexp(ld_as<df>(V[k + (size_t)j * ldV])));
+      for (int k = lane; k < m; k += 32) {
+        if constexpr (X64)
+          be = max(be, (int)((__double_as_longlong((double)V[k + (size_t)j * ldV]) >> 52) & 0x7FF));
+        else
+          be = max(be, oz_bexp(ld_as<df>(V[k + (size_t)j * ldV])));
+      }
     for (int o = 16; o; o >>= 1) be = max(be, __shfl_xor_sync(0xffffffffu, be, o));
     if (lane == 0) Fe[j] = be;
   }
@@ -102,17 +113,24 @@ k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
     const int ln = idx & 31, nt = (idx >> 5) % NT, kk = idx / (32 * NT);
     const int j = 8 * nt + (ln >> 2);
     const int k0 = 16 * kk + 2 * (ln & 3);
-    const float sc = oz_inv_scale(Fe[j]);
-    float d[4][6];
+    float d[4][7];
     const int ks[4] = {k0, k0 + 1, k0 + 8, k0 + 9};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const df v = (j < r && ks[q] < m) ? ld_as<df>(V[ks[q] + (size_t)j * ldV]) : Tr<df>::zero();
-      oz_digits(v, sc, d[q]);
+      const bool in = j < r && ks[q] < m;
+      if constexpr (X64) {
+        oz64_digits(in ? (double)V[ks[q] + (size_t)j * ldV] : 0.0, Fe[j], d[q]);
+      } else {
+        const df v = in ? ld_as<df>(V[ks[q] + (size_t)j * ldV]) : Tr<df>::zero();
+        float d6[6];
+        oz_digits(v, oz_inv_scale(Fe[j]), d6);
+#pragma unroll
+        for (int b = 0; b < 6; ++b) d[q][b] = d6[b];
+      }
     }
 #pragma unroll
-    for (int b = 0; b < 6; ++b)
-      Bf[((size_t)(kk * 6 + b) * NT + nt) * 32 + ln] =
+    for (int b = 0; b < ND; ++b)
+      Bf[((size_t)(kk * ND + b) * NT + nt) * 32 + ln] =
           make_uint2(oz_pack(d[0][b], d[1][b]), oz_pack(d[2][b], d[3][b]));
   }
   __syncthreads();
@@ -179,38 +197,76 @@ k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
     }
     const int be0 = oz_bexp_of(key0, (S*)nullptr, rd.sh), be1 = oz_bexp_of(key1, (S*)nullptr, rd.sh);
     const float sc0 = oz_inv_scale(be0), sc1 = oz_inv_scale(be1);
+    // X64: the rows' largest biased FP64 exponent fields
+    const int eM0 = (int)(key0 >> 20), eM1 = (int)(key1 >> 20);
 
-    float acc[6][NT][4];
+    float acc[ND][NT][4];
 #pragma unroll
-    for (int L = 0; L < 6; ++L)
+    for (int L = 0; L < ND; ++L)
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) acc[L][nt][0] = acc[L][nt][1] = acc[L][nt][2] = acc[L][nt][3] = 0.f;
 
     for (int kk = 0; kk < kt; ++kk) {
       // digits of this lane's 8 values: dq[q][row half][digit], q = k offset 0, 1, 8, 9
-      float dd[4][2][6];
+      float dd[4][2][7];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int k = 16 * kk + 2 * tq + (q & 1) + 8 * (q >> 1);
         const S* c = reinterpret_cast<const S*>(buf + (size_t)(k < m ? k : 0) * OZ_CS);
-        const df x0 = k < m ? rd(c[rg]) : Tr<df>::zero();
-        const df x1 = k < m ? rd(c[rg + 8]) : Tr<df>::zero();
-        oz_digits(x0, sc0, dd[q][0]);
-        oz_digits(x1, sc1, dd[q][1]);
+        if constexpr (X64) {
+          oz64_digits(k < m ? (double)c[rg] : 0.0, eM0, dd[q][0]);
+          oz64_digits(k < m ? (double)c[rg + 8] : 0.0, eM1, dd[q][1]);
+        } else {
+          const df x0 = k < m ? rd(c[rg]) : Tr<df>::zero();
+          const df x1 = k < m ? rd(c[rg + 8]) : Tr<df>::zero();
+          float d0[6], d1[6];
+          oz_digits(x0, sc0, d0);
+          oz_digits(x1, sc1, d1);
+#pragma unroll
+          for (int a = 0; a < 6; ++a) {
+            dd[q][0][a] = d0[a];
+            dd[q][1][a] = d1[a];
+          }
+        }
       }
 #pragma unroll
-      for (int a = 0; a < 6; ++a) {
+      for (int a = 0; a < ND; ++a) {
         const uint32_t af[4] = {oz_pack(dd[0][0][a], dd[1][0][a]), oz_pack(dd[0][1][a], dd[1][1][a]),
                                 oz_pack(dd[2][0][a], dd[3][0][a]), oz_pack(dd[2][1][a], dd[3][1][a])};
-        // b = 1 .. 6 - a (0-based: digit a pairs with b while a + b <= 5), level L = a + b
+        // b = 0 .. ND-1-a (0-based: digit a pairs with b while a + b <= ND - 1), level a + b
 #pragma unroll
-        for (int b = 0; b + a <= 5; ++b)
+        for (int b = 0; b + a <= ND - 1; ++b)
 #pragma unroll
           for (int nt = 0; nt < NT; ++nt)
-            oz_mma(acc[a + b][nt], af, Bf[((size_t)(kk * 6 + b) * NT + nt) * 32 + lane]);
+            oz_mma(acc[a + b][nt], af, Bf[((size_t)(kk * ND + b) * NT + nt) * 32 + lane]);
       }
     }
 
+    if constexpr (X64) {
+      // Y = 2^(eM + fM - 2082) (S_hi + 2^-24 S_lo) with the exact level sums (levels
+      // l = 0..6 at weights 2^(24 - 8l) in S_hi, l = 4..6 at 2^(48 - 8l) in S_lo)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int j = 8 * nt + 2 * tq + (h & 1);
+          const int64_t row = r0 + rg + 8 * (h >> 1);
+          if (j >= r || row >= rows) continue;
+          long long shi = 0, slo = 0;
+#pragma unroll
+          for (int l = 0; l < 4; ++l) shi = (shi << 8) + (long long)__float2int_rn(acc[l][nt][h]);
+#pragma unroll
+          for (int l = 4; l < 7; ++l) slo = (slo << 8) + (long long)__float2int_rn(acc[l][nt][h]);
+          const double t = __fma_rn((double)slo, 0x1p-24, (double)shi);
+          const int e = ((h >> 1) ? eM1 : eM0) + Fe[j] - 2082;
+          // 2^e as two exact powers of two inside FP64's normal range (0 far below it)
+          const int e1 = e / 2, e2 = e - e / 2;
+          const double p1 = e1 < -1022 ? 0.0 : __longlong_as_double((long long)(e1 + 1023) << 52);
+          const double p2 = e2 < -1022 ? 0.0 : __longlong_as_double((long long)(e2 + 1023) << 52);
+          Y[row + (int64_t)j * ldy] = st_as<SO>((double)(t * p1 * p2));
+        }
+      }
+    } else {
     // Y = 2^(E + F) sum_L acc_L 2^(2 - 8L), L = 2..7 (index L - 2), smallest level first
     const int E0 = be0 - 126, E1 = be1 - 126;
 #pragma unroll
@@ -235,6 +291,7 @@ k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restri
         }
         Y[row + (int64_t)j * ldy] = st_as<SO>(df_norm(s, err));
       }
+    }
     }
     // everyone is done reading this buffer (generic proxy) before a bulk copy
     // (async proxy) refills it
@@ -262,27 +319,34 @@ bool tsmm_oz_ok(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max) {
   // 2^24 x 64 -> 10 (8.6) 6.2 vs 4.7 ms; 2^21 x 80 -> 10 (8.9) 0.96 vs 0.87 ms.
   const int mode = tune_get("tsmm.oz", 1);
   if (mode == 0) return false;
+  if (m_max < 1 || m_max > OZ_MAXM || r_max < 1 || r_max > OZ_MAXR) return false;
+  if (comp == Fmt::F64) {
+    // the FP64-accurate form (native FP64 arithmetic): FP64 W, V and Y; "tsmm.oz64" [1].
+    // Worth it wherever the FP64 pipe would do m multiply-adds per output (m >= 16).
+    return tune_get("tsmm.oz64", 1) != 0 && m_max >= 16 && in == Fmt::F64 && vfmt == Fmt::F64 &&
+           out == Fmt::F64;
+  }
   if (mode == 1 && (m_max < 16 || m_max * r_max < 6 * (m_max + r_max))) return false;
   if (comp != Fmt::DF) return false;
   const bool types = (in == Fmt::F64 && vfmt == Fmt::DF && out == Fmt::DF) ||
                      (in == Fmt::DF && vfmt == Fmt::DF && out == Fmt::DF) ||
                      (in == Fmt::F64 && vfmt == Fmt::F64 && out == Fmt::F64);
-  if (!types) return false;
-  return m_max >= 1 && m_max <= OZ_MAXM && r_max >= 1 && r_max <= OZ_MAXR;
+  return types;
 }
 
-size_t tsmm_oz_smem(int m_max, int r_max, int nbuf) {
+size_t tsmm_oz_smem(int m_max, int r_max, int nbuf, bool x64) {
   const int nt = r_max <= 8 ? 1 : (r_max <= 16 ? 2 : 4);
   const int kt = (m_max + 15) / 16;
-  return nbuf * (size_t)m_max * OZ_CS + (size_t)kt * 6 * nt * 32 * sizeof(uint2) + 8 * nt * sizeof(int) + 16;
+  const int nd = x64 ? 7 : 6;
+  return nbuf * (size_t)m_max * OZ_CS + (size_t)kt * nd * nt * 32 * sizeof(uint2) + 8 * nt * sizeof(int) + 16;
 }
 
 namespace {
-template <int NT, class S, class VS, class SO>
+template <int NT, class S, class VS, class SO, bool X64 = false>
 cudaError_t run_oz(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, const int* m_dev,
                    const void* V, int ldV, const int* r_dev, void* Y, int64_t ldy, int* status,
                    cudaStream_t s) {
-  auto k = k_tsmm_oz<NT, S, VS, SO>;
+  auto k = k_tsmm_oz<NT, X64, S, VS, SO>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
   if (e != cudaSuccess) return e;
   k<<<(unsigned)c.ctas, OZ_THREADS, c.smem, s>>>(static_cast<const S*>(W), rows, ld, m_dev, c.m_max,
@@ -292,19 +356,21 @@ cudaError_t run_oz(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, co
   return cudaGetLastError();
 }
 
-template <class S, class VS, class SO>
+template <class S, class VS, class SO, bool X64 = false>
 cudaError_t run_oz_nt(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, const int* m_dev,
                       const void* V, int ldV, const int* r_dev, void* Y, int64_t ldy, int* status,
                       cudaStream_t s) {
-  if (c.r_max <= 8) return run_oz<1, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-  if (c.r_max <= 16) return run_oz<2, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
-  return run_oz<4, S, VS, SO>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+  if (c.r_max <= 8) return run_oz<1, S, VS, SO, X64>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+  if (c.r_max <= 16) return run_oz<2, S, VS, SO, X64>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+  return run_oz<4, S, VS, SO, X64>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
 }
 }  // namespace
 
 cudaError_t launch_tsmm_oz(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
                            const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
                            int64_t ldy, int* status, cudaStream_t s) {
+  if (c.comp == Fmt::F64 && c.in == Fmt::F64 && c.vfmt == Fmt::F64 && c.out == Fmt::F64)
+    return run_oz_nt<double, double, double, true>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
   if (c.in == Fmt::F64 && c.vfmt == Fmt::DF && c.out == Fmt::DF)
     return run_oz_nt<double, df, df>(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
   if (c.in == Fmt::DF && c.vfmt == Fmt::DF && c.out == Fmt::DF)

@@ -19,7 +19,8 @@ import torch
 
 from oracle import tt_svd_oracle as O
 from paper_2102_00104_gb300 import api
-from tests.gpu_common import ensure_lib
+from paper_2102_00104_gb300 import inputs
+from tests.gpu_common import ensure_lib, tt_full_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -81,3 +82,40 @@ def test_full_size_8p10_fp32_form_rmax32():
     d = Xh - Xt
     nx2 = float(np.trace(G))
     assert abs(float(np.dot(d, d)) - res.err2) <= 1e-5 * nx2
+
+
+@pytest.mark.parametrize("r_max,arith", [(20, "f64"), (50, "df")])
+def test_full_size_8p10_planted_rank16(r_max, arith):
+    # the second input of the 8^10 configuration: planted TT rank 16 (Gaussian cores,
+    # ||X||_F = 1) plus Gaussian noise of norm 1e-6, built on the device with bench.py's seed.
+    # References formed on the device with library routines (FP64 Householder QR of the
+    # 2^24 x 64 unfolding, then the singular values of its R), which keep the small noise
+    # singular values that a Gram matrix would lose
+    ensure_lib()
+    dims = (8,) * 10
+    X = inputs.planted_tt_device(dims, 16, 1, noise_rel=1e-6)
+    plan = api.TTSVDPlan(dims, r_max, 0.0, torch.float64, arith, want_sigma=True)
+    plan.run(X)
+    res = plan.result()
+    assert res.ranks == O.planned_ranks(list(dims), r_max)
+
+    M = X.view(64, 8 ** 8)  # row c = column c of the unfolding X_(8) (Fortran order)
+    R = torch.linalg.qr(M.t(), mode="r").R
+    del M
+    s_ref = torch.linalg.svdvals(R).cpu().numpy()
+    nx2 = float(torch.dot(X, X).item())
+    # the planted structure: 16 values carry the tensor, the rest the noise
+    assert s_ref[15] > 1e-3 * s_ref[0] and s_ref[16] < 1e-5 * s_ref[0]
+    got = res.sigma[9].cpu().numpy()[:64]
+    assert np.max(np.abs(got - s_ref)) <= 1e-12 * s_ref[0], np.max(np.abs(got - s_ref))
+    assert abs(float(np.sum(got ** 2)) - nx2) <= 1e-12 * nx2
+
+    for c in res.core_arrays()[1:]:
+        assert O.core_orthonormality_defect(c) <= 1e-13 * 80
+    Xt = tt_full_dev([c.to(torch.float64) for c in res.cores], dims)
+    d = X - Xt
+    del Xt
+    err2 = float(torch.dot(d, d).item())
+    assert abs(err2 - res.err2) <= 1e-12 * nx2, (err2, res.err2, nx2)
+    # rank >= 16 keeps the planted part: only noise is discarded, 9 steps at most 1e-12 each
+    assert err2 <= 9e-12 * nx2, err2 / nx2
