@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--serve-seconds", type=float, default=4.0)
     p.add_argument("--case", default="", help="one building block for profiling instead of the bench: "
-                   "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix), "
+                   "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix), tsqr64:ROWS:M (native FP64), "
                    "tsmm:ROWS:M:K (W V(:, 0:K) of a uniform FP64 W) or svd:M (small SVD of a "
                    "uniform upper-triangular R) or ttsvd:N:D:RMAX:ARITH (a whole TT-SVD of a "
                    "uniform N^D FP64 tensor, ARITH f64 or df), each optionally followed by "
@@ -263,6 +263,17 @@ def run_case(spec: str) -> int:
         wp = (work.data_ptr() + 255) & ~255
         call = lambda: capi.tt_tsqr(W.data_ptr(), capi.TT_F64, rows, m, rows, R.data_ptr(), wp, wb,
                                     int(s.cuda_stream))
+    elif parts[0] == "tsqr64":
+        # tsqr64:ROWS:M -- the native FP64 TSQR (tt_tsqr_ex) of a uniform FP64 matrix
+        rows, m = int(parts[1]), int(parts[2])
+        W = api.gen_uniform(rows * m, 3, torch.float64)
+        R = torch.empty(m * m, dtype=torch.float64, device="cuda")
+        wb = capi.tt_tsqr_query(rows, m, capi.TT_F64)
+        work = torch.empty(wb + 256, dtype=torch.uint8, device="cuda")
+        wp = (work.data_ptr() + 255) & ~255
+        call = lambda: capi.check(capi.lib().tt_tsqr_ex(W.data_ptr(), capi.TT_F64, rows, m, rows, R.data_ptr(),
+                                                        wp, wb, capi.TT_ARITH_F64, int(s.cuda_stream)),
+                                  "tt_tsqr_ex")
     elif parts[0] == "tsmm":
         rows, m, k = int(parts[1]), int(parts[2]), int(parts[3])
         W = api.gen_uniform(rows * m, 3, torch.float64)

@@ -180,6 +180,12 @@ tt_status tt_last_device_status(const void* work, void* stream);
 tt_status tt_tsqr_query(int64_t rows, int m, tt_dtype dt, size_t* work_bytes);
 tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, double* R_out,
                   void* work, size_t work_bytes, void* stream);
+/* tt_tsqr in a chosen arithmetic: TT_ARITH_F64 with dt = TT_F64 runs every level in native
+ *   FP64 (the native FP64 form of tt_svd; up to m = 64 the first level may take the blocked
+ *   kernel, tuning key tsqr.blk64); any other arith is tt_tsqr.  Same workspace
+ *   (tt_tsqr_query covers both arithmetics). */
+tt_status tt_tsqr_ex(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, double* R_out,
+                     void* work, size_t work_bytes, tt_arith arith, void* stream);
 
 /* tt_small_svd: R = U Sigma V^T for a square m x m matrix R (column-major,
  *   device doubles) by one-sided Jacobi (Eq. QR_trick needs Sigma and V only).

@@ -154,16 +154,19 @@ def gen_uniform(count: int, seed: int, dtype=torch.float64, start: int = 0, devi
     return out
 
 
-def tsqr(W: torch.Tensor, stream=None) -> torch.Tensor:
+def tsqr(W: torch.Tensor, stream=None, arith: str = "df") -> torch.Tensor:
     """R (m x m, FP64, upper triangular) of the Q-less TSQR of W.
-    W: CUDA tensor of shape (m, rows), i.e. the column-major rows x m matrix."""
+    W: CUDA tensor of shape (m, rows), i.e. the column-major rows x m matrix.  arith "f64"
+    with an FP64 W: every level in native FP64 (tt_tsqr_ex)."""
     m, rows = W.shape
     dt = _DT[W.dtype]
     wb = capi.tt_tsqr_query(rows, m, dt)
     work = torch.empty(wb + 256, dtype=torch.uint8, device=W.device)
     wp = (work.data_ptr() + 255) & ~255
     R = torch.empty(m, m, dtype=torch.float64, device=W.device)  # R^T in C order
-    capi.tt_tsqr(W.data_ptr(), dt, rows, m, W.stride(0), R.data_ptr(), wp, wb, _stream_ptr(stream))
+    ar = capi.TT_ARITH_F64 if arith == "f64" else capi.TT_ARITH_DF
+    capi.check(capi.lib().tt_tsqr_ex(W.data_ptr(), dt, rows, m, W.stride(0), R.data_ptr(), wp, wb, ar,
+                                     _stream_ptr(stream)), "tt_tsqr_ex")
     capi.check(capi.tt_last_device_status(wp, _stream_ptr(stream)), "tt_tsqr (device)")
     return R.t()
 

@@ -27,7 +27,7 @@ EXPORTED = ["tt_query", "tt_core_caps", "tt_svd", "tt_svd_ex", "tt_last_device_s
             "tt_serve_submit", "tt_serve_poll", "tt_serve_release", "tt_serve_destroy", "tt_status_str",
             "tt_profile", "tt_profile_read", "tt_stats", "tt_last_error", "tt_small_svd_noalloc", "tt_tune_set",
             "tt_query_from_host", "tt_svd_from_host", "tt_query_ex", "tt_range_rule", "tt_fma_rate",
-            "tt_wait_selftest", "tt_tsmm_ex"]
+            "tt_wait_selftest", "tt_tsmm_ex", "tt_tsqr_ex"]
 
 
 class tt_opts(C.Structure):
@@ -103,6 +103,8 @@ _SIGS = {
     "tt_range_rule": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tt_fma_rate": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
     "tt_wait_selftest": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    "tt_tsqr_ex": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_int64, C.c_void_p, C.c_void_p,
+                             C.c_size_t, C.c_int, C.c_void_p]),
     "tt_tsmm_ex": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_int64, C.c_void_p, C.c_int,
                              C.c_void_p, C.c_int64, C.c_int, C.c_void_p]),
 }

@@ -1254,33 +1254,44 @@ tt_status tt_last_device_status(const void* work, void* stream) {
 // ---- building blocks ------------------------------------------------------------------
 static Fmt tsqr_comp2(tt_dtype) { return Fmt::DF; }
 
+// the TSQR levels of tt_tsqr / tt_tsqr_ex: FP64 input in float-float, or all levels in
+// native FP64 (native = true)
+static std::vector<TsqrLevel> tsqr_api_plan(int64_t rows, int m, tt_dtype dt, bool native) {
+  const Fmt in = dt == TT_F32 ? Fmt::F32 : Fmt::F64;
+  const Fmt c1 = dt == TT_F32 ? Fmt::F32 : (native ? Fmt::F64 : Fmt::DF);
+  return plan_tsqr(rows, m, in, c1, native ? Fmt::F64 : tsqr_comp2(dt), num_sms(), 0);
+}
+
 tt_status tt_tsqr_query(int64_t rows, int m, tt_dtype dt, size_t* work_bytes) {
   if (rows < 1 || m < 1 || m > kMaxM || (dt != TT_F64 && dt != TT_F32) || !work_bytes)
     return TT_EINVAL;
-  const Fmt in = dt == TT_F32 ? Fmt::F32 : Fmt::F64;
-  const Fmt c1 = dt == TT_F32 ? Fmt::F32 : Fmt::DF;
-  auto lv = plan_tsqr(rows, m, in, c1, tsqr_comp2(dt), num_sms(), 0);
-  if (lv.empty()) return TT_ENOTIMPL;
   size_t szR = 0, scr = 0;
-  for (auto& L : lv) {
-    szR = std::max(szR, (size_t)L.warps * L.mb * m * fmt_bytes(L.out));
-    scr = std::max(scr, tsqr_wide_scratch_bytes(L));
+  // FP64 input: room for either arithmetic (tt_tsqr_ex)
+  for (int native = 0; native <= (dt == TT_F64 ? 1 : 0); ++native) {
+    auto lv = tsqr_api_plan(rows, m, dt, native != 0);
+    if (lv.empty()) return TT_ENOTIMPL;
+    for (auto& L : lv) {
+      szR = std::max(szR, (size_t)L.warps * L.mb * m * fmt_bytes(L.out));
+      scr = std::max(scr, tsqr_wide_scratch_bytes(L));
+    }
   }
   *work_bytes = align256(256) + 2 * align256(szR) + align256(scr);
   return TT_OK;
 }
 
-tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, double* R_out,
-                  void* work, size_t work_bytes, void* stream) {
+tt_status tt_tsqr_ex(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, double* R_out,
+                     void* work, size_t work_bytes, tt_arith arith, void* stream) {
   size_t need = 0;
   tt_status st = tt_tsqr_query(rows, m, dt, &need);
   if (st != TT_OK) return st;
-  if (!W || !R_out || !work || ld < rows || ((uintptr_t)work & 255)) return TT_EINVAL;
+  if (!W || !R_out || !work || ld < rows || ((uintptr_t)work & 255) ||
+      (arith != TT_ARITH_AUTO && arith != TT_ARITH_DF && arith != TT_ARITH_F64))
+    return TT_EINVAL;
   if (work_bytes < need) return TT_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
   const Fmt in = dt == TT_F32 ? Fmt::F32 : Fmt::F64;
-  const Fmt c1 = dt == TT_F32 ? Fmt::F32 : Fmt::DF;
-  auto lv = plan_tsqr(rows, m, in, c1, tsqr_comp2(dt), num_sms(), 0);
+  const bool native = dt == TT_F64 && arith == TT_ARITH_F64;
+  auto lv = tsqr_api_plan(rows, m, dt, native);
   size_t szR = 0;
   for (auto& L : lv) szR = std::max(szR, (size_t)L.warps * L.mb * m * fmt_bytes(L.out));
   char* wb = static_cast<char*>(work);
@@ -1288,8 +1299,9 @@ tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, d
   int* status = reinterpret_cast<int*>(wb);
   XRange* xr = reinterpret_cast<XRange*>(wb + 16);
   TT_CK(cudaMemsetAsync(wb, 0, 256, s));
-  // (a strided W: the first pass starts unshifted and is redone if that was wrong)
-  if (ld == rows) TT_CK(launch_range_sample(in, W, rows * (int64_t)m, xr, s));
+  // (a strided W: the first pass starts unshifted and is redone if that was wrong; native
+  // FP64 needs no exponent shift)
+  if (ld == rows && !native) TT_CK(launch_range_sample(in, W, rows * (int64_t)m, xr, s));
   char* R0 = wb + align256(256);
   char* R1 = R0 + align256(szR);
   char* scr = R1 + align256(szR);
@@ -1302,7 +1314,7 @@ tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, d
     void* Rout = (l & 1) ? R1 : R0;
     const int64_t ldR = lv[l].warps * lv[l].mb;
     TsqrLevel L = lv[l];
-    if (l == 0) L.xr = xr;
+    if (l == 0 && !native) L.xr = xr;
     TT_CK(launch_tsqr_level(L, lin, lld, nullptr, Rout, ldR, scr, status, s));
     ++g_launches;
     if (L.xr) {
@@ -1317,9 +1329,14 @@ tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, d
     ldRfin = ldR;
     rf = lv[l].out;
   }
-  // R of W = 2^k times the R of the shifted W
-  g_launches += 2;  // the sample and the copy
+  // R of W = 2^k times the R of the shifted W (k = 0 for native FP64: xr is zeroed)
+  g_launches += native ? 1 : 2;  // the sample and the copy
   return cuda_err(launch_copy_mat_f64(rf, Rfin, ldRfin, m, m, 1, R_out, m, s, xr));
+}
+
+tt_status tt_tsqr(const void* W, tt_dtype dt, int64_t rows, int m, int64_t ld, double* R_out,
+                  void* work, size_t work_bytes, void* stream) {
+  return tt_tsqr_ex(W, dt, rows, m, ld, R_out, work, work_bytes, TT_ARITH_DF, stream);
 }
 
 tt_status tt_small_svd_query(int m, size_t* work_bytes) {
