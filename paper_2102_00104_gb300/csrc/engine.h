@@ -118,9 +118,11 @@ size_t tsqr_col_smem(int m_max, Fmt comp, int id);
 cudaError_t launch_tsqr_col(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
                             void* Rout, int64_t ldR, int* status, cudaStream_t s);
 // kind 3, layout id 15: the blocked native-FP64 kernel (compact-WY blocks of 8 reflectors,
-// trailing updates on the tensor cores; m <= 64, 128-row panels, 2 CTAs per SM)
+// trailing updates on the tensor cores; m <= 64 with 128-row panels, m <= 80 with 96-row
+// panels, 2 CTAs per SM)
 constexpr int kTsqrBlkId = 15;
-size_t tsqr_blk_smem();
+size_t tsqr_blk_smem(int m_max);
+int tsqr_blk_rows(int m_max);
 cudaError_t launch_tsqr_blk(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
                             void* Rout, int64_t ldR, int* status, cudaStream_t s);
 // kind 4 (shared-memory panels, R in an L2-resident global slice per CTA): rows per lane or -1

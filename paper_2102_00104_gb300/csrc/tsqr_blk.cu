@@ -33,21 +33,23 @@
 namespace tt {
 namespace blk {
 
-constexpr int PB = 128;        // rows per panel
+// Layouts: (MX = largest m, PB = rows per panel) = (64, 128) and (80, 96), both two CTAs
+// per SM.  The chain holds PB / 32 rows per lane; the panel product takes PB / 16 k-steps.
 constexpr int NW = 8;          // warps per CTA (two CTAs per SM)
 constexpr int NT = NW * 32;
 constexpr int KB = 8;          // reflectors per block
-constexpr int MX = 64;         // largest m
 constexpr int NLV = 7;         // digit levels kept
-constexpr int RPL = PB / 32;   // rows per lane in the chain
 
 // panel value (r, c) at r * MX + (c ^ swz(r)): conflict-free for a warp reading a column
 // (lane -> row) and for the mma fragments of the panel product (lane -> (column, row pair))
 __device__ __forceinline__ int swz(int r) { return ((r & 7) << 1) | ((r >> 3) & 1); }
+template <int MX>
 __device__ __forceinline__ int pix(int r, int c) { return r * MX + (c ^ swz(r)); }
 // packed upper triangle of R, row-major
+template <int MX>
 __device__ __forceinline__ int rix(int i, int c) { return i * MX - (i * (i - 1)) / 2 + (c - i); }
 
+template <int MX, int PB>
 struct Smem {
   double P[PB * MX];
   double R[MX * (MX + 1) / 2];
@@ -62,7 +64,8 @@ struct Smem {
   int abort_flag;
 };
 
-__host__ __device__ constexpr size_t smem_bytes() { return sizeof(Smem); }
+template <int MX, int PB>
+__host__ __device__ constexpr size_t smem_bytes() { return sizeof(Smem<MX, PB>); }
 
 // ---- FP64-accurate digits ------------------------------------------------------------
 // u = floor(|x| 2^(1078 - em)) < 2^56 for |x| < 2^(em - 1022), as (hi: 24 bits, lo: 32 bits)
@@ -133,11 +136,13 @@ __device__ __forceinline__ double scale2(double x, int e) {
 // ---- phase 1: the reflector chain of one block ---------------------------------------
 // warp i (< kb) owns column j = j0 + i: applies the block's earlier reflectors as they are
 // published, then forms and publishes its own
-__device__ __forceinline__ bool chain(Smem& S, int j0, int i, int lane, uint32_t par, int* status) {
+template <int MX, int PB>
+__device__ __forceinline__ bool chain(Smem<MX, PB>& S, int j0, int i, int lane, uint32_t par, int* status) {
+  constexpr int RPL = PB / 32;
   const int j = j0 + i;
   double a[RPL];
 #pragma unroll
-  for (int q = 0; q < RPL; ++q) a[q] = S.P[pix(lane + 32 * q, j)];
+  for (int q = 0; q < RPL; ++q) a[q] = S.P[pix<MX>(lane + 32 * q, j)];
   for (int jj = 0; jj < i; ++jj) {
     const int jp = j0 + jj;
     if (!colk::mbar_wait(reinterpret_cast<uint64_t*>(&S.bar[jp]), par)) {
@@ -149,33 +154,35 @@ __device__ __forceinline__ bool chain(Smem& S, int j0, int i, int lane, uint32_t
     }
     double x[RPL];
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) x[q] = S.P[pix(lane + 32 * q, jp)];
+    for (int q = 0; q < RPL; ++q) x[q] = S.P[pix<MX>(lane + 32 * q, jp)];
     const double piv = S.piv[jp], rt = S.rt[jp];
     double d0 = 0.0, d1 = 0.0;
 #pragma unroll
-    for (int q = 0; q < RPL; q += 2) {
+    for (int q = 0; q + 1 < RPL; q += 2) {
       d0 = fma(x[q], a[q], d0);
       d1 = fma(x[q + 1], a[q + 1], d1);
     }
+    if constexpr (RPL % 2) d0 = fma(x[RPL - 1], a[RPL - 1], d0);
     const double d = colk::warp_allsum<double>(d0 + d1);
-    const double r = S.R[rix(jp, j)];
+    const double r = S.R[rix<MX>(jp, j)];
     const double c = fma(piv, r, d) * rt;
-    if (lane == 0) S.R[rix(jp, j)] = fma(-c, piv, r);
+    if (lane == 0) S.R[rix<MX>(jp, j)] = fma(-c, piv, r);
 #pragma unroll
     for (int q = 0; q < RPL; ++q) a[q] = fma(-c, x[q], a[q]);
   }
   double n0 = 0.0, n1 = 0.0;
 #pragma unroll
-  for (int q = 0; q < RPL; q += 2) {
+  for (int q = 0; q + 1 < RPL; q += 2) {
     n0 = fma(a[q], a[q], n0);
     n1 = fma(a[q + 1], a[q + 1], n1);
   }
+  if constexpr (RPL % 2) n0 = fma(a[RPL - 1], a[RPL - 1], n0);
   const double D = colk::warp_allsum<double>(n0 + n1);
-  const Refl<double> h = householder(S.R[rix(j, j)], D, Tr<double>::eps());
+  const Refl<double> h = householder(S.R[rix<MX>(j, j)], D, Tr<double>::eps());
   int em = 0;
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
-    S.P[pix(lane + 32 * q, j)] = a[q];
+    S.P[pix<MX>(lane + 32 * q, j)] = a[q];
     em = max(em, efield(a[q]));
   }
 #pragma unroll
@@ -183,7 +190,7 @@ __device__ __forceinline__ bool chain(Smem& S, int j0, int i, int lane, uint32_t
   if (lane == 0) {
     S.piv[j] = h.piv;
     S.rt[j] = h.rt;
-    S.R[rix(j, j)] = h.alpha;
+    S.R[rix<MX>(j, j)] = h.alpha;
     S.colE[j] = em;
   }
   __syncwarp();
@@ -196,7 +203,8 @@ __device__ __forceinline__ bool chain(Smem& S, int j0, int i, int lane, uint32_t
 // Warp w takes m-tile w % mt and the k-steps w / mt, + nkc, ...  (at most four: the sums of
 // one level over two k-steps stay below 2^24, so the FP32 accumulators are emptied into
 // integers every two k-steps)
-__device__ __forceinline__ void prod1(Smem& S, int j0, int m, int w, int lane) {
+template <int MX, int PB>
+__device__ __forceinline__ void prod1(Smem<MX, PB>& S, int j0, int m, int w, int lane) {
   const int g = lane >> 2, t = lane & 3;
   const int M1 = m - j0;
   const int mt = (M1 + 15) >> 4;
@@ -224,10 +232,10 @@ __device__ __forceinline__ void prod1(Smem& S, int j0, int m, int w, int lane) {
     uint32_t A[NLV][4], B[NLV][2];
     {
       uint32_t d[NLV];
-      const double v00 = in0 ? S.P[pix(r0, ca0)] : 0.0, v01 = in0 ? S.P[pix(r0 + 1, ca0)] : 0.0;
-      const double v10 = in1 ? S.P[pix(r0, ca1)] : 0.0, v11 = in1 ? S.P[pix(r0 + 1, ca1)] : 0.0;
-      const double v20 = in0 ? S.P[pix(r0 + 8, ca0)] : 0.0, v21 = in0 ? S.P[pix(r0 + 9, ca0)] : 0.0;
-      const double v30 = in1 ? S.P[pix(r0 + 8, ca1)] : 0.0, v31 = in1 ? S.P[pix(r0 + 9, ca1)] : 0.0;
+      const double v00 = in0 ? S.P[pix<MX>(r0, ca0)] : 0.0, v01 = in0 ? S.P[pix<MX>(r0 + 1, ca0)] : 0.0;
+      const double v10 = in1 ? S.P[pix<MX>(r0, ca1)] : 0.0, v11 = in1 ? S.P[pix<MX>(r0 + 1, ca1)] : 0.0;
+      const double v20 = in0 ? S.P[pix<MX>(r0 + 8, ca0)] : 0.0, v21 = in0 ? S.P[pix<MX>(r0 + 9, ca0)] : 0.0;
+      const double v30 = in1 ? S.P[pix<MX>(r0 + 8, ca1)] : 0.0, v31 = in1 ? S.P[pix<MX>(r0 + 9, ca1)] : 0.0;
       digits2(v00, ema0, v01, ema0, d);
 #pragma unroll
       for (int a = 0; a < NLV; ++a) A[a][0] = d[a];
@@ -240,10 +248,10 @@ __device__ __forceinline__ void prod1(Smem& S, int j0, int m, int w, int lane) {
       digits2(v30, ema1, v31, ema1, d);
 #pragma unroll
       for (int a = 0; a < NLV; ++a) A[a][3] = d[a];
-      digits2(S.P[pix(r0, cb)], emb, S.P[pix(r0 + 1, cb)], emb, d);
+      digits2(S.P[pix<MX>(r0, cb)], emb, S.P[pix<MX>(r0 + 1, cb)], emb, d);
 #pragma unroll
       for (int b = 0; b < NLV; ++b) B[b][0] = d[b];
-      digits2(S.P[pix(r0 + 8, cb)], emb, S.P[pix(r0 + 9, cb)], emb, d);
+      digits2(S.P[pix<MX>(r0 + 8, cb)], emb, S.P[pix<MX>(r0 + 9, cb)], emb, d);
 #pragma unroll
       for (int b = 0; b < NLV; ++b) B[b][1] = d[b];
     }
@@ -290,12 +298,14 @@ __device__ __forceinline__ double level_value(const int (&s)[NLV], int e) {
 // scalings, folded into the digit exponents): A = X D^-1 with one exponent per row, B = D Z
 // with one exponent per column (zE, formed with the same scaling)
 __device__ __forceinline__ int ef1(double x) { return x != 0.0 ? max(efield(x), 1) : 0; }
-__device__ __forceinline__ void prod2(Smem& S, int j0, int m, int w, int lane) {
+template <int MX, int PB>
+__device__ __forceinline__ void prod2(Smem<MX, PB>& S, int j0, int m, int w, int lane) {
+  if (w >= PB / 16) return;  // one 16-row m-tile per warp
   const int g = lane >> 2, t = lane & 3;
   const int ra = 16 * w + g, rb = ra + 8;
   const int E0 = max(S.colE[j0 + 2 * t], 1), E1 = max(S.colE[j0 + 2 * t + 1], 1);
-  const double xa0 = S.P[pix(ra, j0 + 2 * t)], xa1 = S.P[pix(ra, j0 + 2 * t + 1)];
-  const double xb0 = S.P[pix(rb, j0 + 2 * t)], xb1 = S.P[pix(rb, j0 + 2 * t + 1)];
+  const double xa0 = S.P[pix<MX>(ra, j0 + 2 * t)], xa1 = S.P[pix<MX>(ra, j0 + 2 * t + 1)];
+  const double xb0 = S.P[pix<MX>(rb, j0 + 2 * t)], xb1 = S.P[pix<MX>(rb, j0 + 2 * t + 1)];
   // exponents of the rows of X D^-1
   auto fa = [](double x, int E) { return x != 0.0 ? ef1(x) - E + 1023 : 0; };
   int ea = max(fa(xa0, E0), fa(xa1, E1)), eb = max(fa(xb0, E0), fa(xb1, E1));
@@ -343,7 +353,7 @@ __device__ __forceinline__ void prod2(Smem& S, int j0, int m, int w, int lane) {
         const long long T = shi * 65536 + (slo >> 8);
         const int e = ((h >> 1) ? eb : ea) + max(S.zE[c], 1) - 2084 - 16;
         const double y = scale2(__ll2double_rn(T), e);
-        const int ix = pix(row, c);
+        const int ix = pix<MX>(row, c);
         const double v = S.P[ix] - y;
         S.P[ix] = v;
         emx[h & 1] = max(emx[h & 1], efield(v));
@@ -366,14 +376,15 @@ __device__ __forceinline__ void prod2(Smem& S, int j0, int m, int w, int lane) {
 }  // namespace blk
 
 // R packed as in the column-owned kernel's output: block blockIdx.x of the stacked R's
-template <class RO>
+template <int MX, int PB, class RO>
 __global__ void __launch_bounds__(blk::NT, 2)
 k_tsqr_blk(const double* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
            int m_val, int mmax, RO* __restrict__ Rout, int64_t ldR, int mb, int64_t npanels,
            int* status) {
   using namespace blk;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  constexpr int RPL = PB / 32;
+  Smem<MX, PB>& S = *reinterpret_cast<Smem<MX, PB>*>(smem_raw);
   const int m = m_ptr ? *m_ptr : m_val;
   if (m < 1 || m > MX || m > mmax || m > mb || blockDim.x != NT) {
     if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
@@ -409,7 +420,7 @@ k_tsqr_blk(const double* __restrict__ W, int64_t rows, int64_t ld, const int* __
           int em = 0;
 #pragma unroll
           for (int q = 0; q < RPL; ++q) {
-            S.P[pix(lane + 32 * q, c)] = v[s][q];
+            S.P[pix<MX>(lane + 32 * q, c)] = v[s][q];
             em = max(em, efield(v[s][q]));
           }
 #pragma unroll
@@ -454,7 +465,7 @@ k_tsqr_blk(const double* __restrict__ W, int64_t rows, int64_t ld, const int* __
         }
         const double val = level_value(s, max(S.colE[j0 + rho], 1) + max(S.colE[j0 + i], 1) - 2084);
         if (rho < KB) S.G[rho * KB + i] = val;
-        else S.Z[i * MX + j0 + rho] = fma(S.piv[j0 + i], S.R[rix(j0 + i, j0 + rho)], val);
+        else S.Z[i * MX + j0 + rho] = fma(S.piv[j0 + i], S.R[rix<MX>(j0 + i, j0 + rho)], val);
       }
       __syncthreads();
       // Z row by row per column (z_i = rt_i (W_i - sum_{i'<i} G_i'i z_i')), the block's R rows;
@@ -469,7 +480,7 @@ k_tsqr_blk(const double* __restrict__ W, int64_t rows, int64_t ld, const int* __
           for (int q = 0; q < i; ++q) acc = fma(-S.G[q * KB + i], z[q], acc);
           z[i] = acc * S.rt[j0 + i];
           S.Z[i * MX + c] = z[i];
-          const int ri = rix(j0 + i, c);
+          const int ri = rix<MX>(j0 + i, c);
           S.R[ri] = fma(-S.piv[j0 + i], z[i], S.R[ri]);
           if (z[i] != 0.0) ez = max(ez, ef1(z[i]) + max(S.colE[j0 + i], 1) - 1023);
         }
@@ -485,19 +496,23 @@ k_tsqr_blk(const double* __restrict__ W, int64_t rows, int64_t ld, const int* __
   if (*reinterpret_cast<volatile int*>(&S.abort_flag)) return;
   for (int idx = tid; idx < mb * m; idx += NT) {
     const int i = idx % mb, k = idx / mb;
-    const double v = (i < m && i <= k) ? S.R[blk::rix(i, k)] : 0.0;
+    const double v = (i < m && i <= k) ? S.R[blk::rix<MX>(i, k)] : 0.0;
     Rout[(int64_t)blockIdx.x * mb + i + (int64_t)k * ldR] = st_as<RO>(v);
   }
 }
 
-size_t tsqr_blk_smem() { return blk::smem_bytes(); }
+size_t tsqr_blk_smem(int m_max) {
+  return m_max <= 64 ? blk::smem_bytes<64, 128>() : blk::smem_bytes<80, 96>();
+}
+int tsqr_blk_rows(int m_max) { return m_max <= 64 ? 128 : 96; }
 
 cudaError_t launch_tsqr_blk(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout,
                             int64_t ldR, int* status, cudaStream_t s) {
-  if (L.in != Fmt::F64 || L.comp != Fmt::F64 || L.out != Fmt::F64 || L.mmax > blk::MX)
+  if (L.in != Fmt::F64 || L.comp != Fmt::F64 || L.out != Fmt::F64 || L.mmax > 80 ||
+      L.pr != tsqr_blk_rows(L.mmax))
     return cudaErrorInvalidValue;
-  auto kern = k_tsqr_blk<double>;
-  const size_t sm = blk::smem_bytes();
+  auto kern = L.mmax <= 64 ? k_tsqr_blk<64, 128, double> : k_tsqr_blk<80, 96, double>;
+  const size_t sm = tsqr_blk_smem(L.mmax);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   // two CTAs per SM: the largest shared-memory carveout

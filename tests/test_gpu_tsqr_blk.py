@@ -33,7 +33,9 @@ def sign_fixed(R):
 # one panel, a ragged panel, several blocks with a partial last block, all CTAs busy,
 # rows < m, and the 2^20 x 64 shape of the benchmark's first level at 1/16 scale
 CASES = [(128, 17), (129, 20), (1000, 24), (4096, 33), (20000, 48), (12345, 63), (100000, 64),
-         (9, 40), (64, 64), (1 << 20, 64)]
+         (9, 40), (64, 64), (1 << 20, 64),
+         # the 96-row layout for 64 < m <= 80 (the m = 80 steps of an 8^d tensor at r_max = 10)
+         (96, 80), (97, 65), (5000, 72), (100000, 80), (30, 80), (1 << 19, 80)]
 
 
 @pytest.mark.parametrize("rows,m", CASES)
@@ -52,11 +54,12 @@ def test_blocked_tsqr_matches_oracle(rows, m):
         assert np.max(np.abs(sign_fixed(R) - sign_fixed(Ro))) <= 1e-12 * nw
 
 
-def test_blocked_equals_column_kernel():
+@pytest.mark.parametrize("m", [64, 80])
+def test_blocked_equals_column_kernel(m):
     # the same FP64 Householder sequence with the block transformations on the tensor cores:
     # R agrees with the column-owned kernel's R to FP64 rounding
     rng = np.random.default_rng(5)
-    W = rng.standard_normal((300000, 64)) + 3.0
+    W = rng.standard_normal((300000, m)) + 3.0
     Rb = api.tsqr(colmajor(W), arith="f64").cpu().numpy()
     capi.tt_tune_set("tsqr.blk64", 0)
     try:
@@ -66,16 +69,16 @@ def test_blocked_equals_column_kernel():
     assert np.max(np.abs(sign_fixed(Rb) - sign_fixed(Rc))) <= 1e-13 * np.linalg.norm(W)
 
 
-@pytest.mark.parametrize("span", [0, 60, 300])
-def test_blocked_tsqr_column_scaling(span):
+@pytest.mark.parametrize("span,m", [(0, 64), (60, 64), (300, 64), (300, 80)])
+def test_blocked_tsqr_column_scaling(span, m):
     # W = G 2^s_c: R(W) = R(G) 2^s_c up to row signs, whatever the exponents
     rng = np.random.default_rng(span + 11)
-    G = rng.standard_normal((50000, 64))
-    s = rng.integers(-span, span + 1, size=64) if span else np.zeros(64, dtype=np.int64)
+    G = rng.standard_normal((50000, m))
+    s = rng.integers(-span, span + 1, size=m) if span else np.zeros(m, dtype=np.int64)
     W = np.ldexp(G, s[None, :])
     R = api.tsqr(colmajor(W), arith="f64").cpu().numpy()
     Rg = np.ldexp(R, -s[None, :])
-    Ro = tsqr_flat(G, 64)
+    Ro = tsqr_flat(G, m)
     assert np.max(np.abs(sign_fixed(Rg) - sign_fixed(Ro))) <= 1e-12 * np.linalg.norm(G)
 
 
@@ -105,9 +108,9 @@ def run_f64(X, r_max):
     return plan.result()
 
 
-@pytest.mark.parametrize("dims,r_max", [((8,) * 7, 8), ((4,) * 9, 6), ((6, 7, 8, 9, 5), 20)])
+@pytest.mark.parametrize("dims,r_max", [((8,) * 7, 8), ((4,) * 9, 6), ((6, 7, 8, 9, 5), 20), ((8,) * 6, 10)])
 def test_tt_svd_native_fp64_with_blocked_tsqr(dims, r_max):
-    # the whole native FP64 path with the blocked first levels (unfoldings of 32..64
+    # the whole native FP64 path with the blocked first levels (unfoldings of 24..80
     # columns), against the Alg. 1 oracle at the FP64 form's bar
     X = uniform_tensor(dims, seed=sum(dims) * r_max)
     res = run_f64(X, r_max)
