@@ -5,8 +5,11 @@
 // column-owned kernel, but the m columns of a panel are taken in blocks of KB = 8:
 //
 //   1. the reflector chain of the block (Alg. 6, column by column) runs on the block's
-//      own columns only: warp i owns column j0 + i (4 rows per lane) and publishes its
-//      reflector (pivot entry, 1/t, the panel part x in shared memory) on an mbarrier;
+//      own columns only: warp w < 4 owns columns j0 + w and j0 + w + 4 (PB / 32 rows per
+//      lane) and publishes each reflector (pivot entry, 1/t, the panel part x in shared
+//      memory) on an mbarrier; the owner of the next pivot column applies the current
+//      pivot to it and publishes before it updates its other column, so the critical
+//      path (one reflector per step) meets no other chain warp's FP64 work;
 //   2. the block's eight reflectors H_i = I - rt_i v_i v_i^T, v_i = [piv_i e_{j0+i}; x_i],
 //      act on the columns right of the block as one transformation (compact WY,
 //      Schreiber & Van Loan 1989): with W = V^T C (W_ic = piv_i R_{j0+i,c} + x_i . P_c)
@@ -133,17 +136,126 @@ __device__ __forceinline__ double scale2(double x, int e) {
   return pow2_split(x, e);
 }
 
+
+// ---- reflector scalars: FP32 seeds refined by FP64 Newton steps ----------------------------
+// A dependent FP64 operation costs ~64 clocks on this part and the library's square root and
+// reciprocal ~10 and ~6 of them; the chain needs one of each per column.  Here the seed is
+// the FP32 approximation (rsqrt.approx / rcp.approx, |error| < 2^-21) of the value scaled
+// into [1, 4) by an exact power of two, and Newton's iteration in FP64 refines it:
+// sqrt: s <- s + (T - s^2) h with h ~ 1/(2 sqrt T) (twice: error ~2^-66 before rounding);
+// reciprocal: r <- r (1 + q + q^2), q = 1 - t r (error ~q^3).  Measured against CUDA's
+// sqrt and division on 2^20 values spread over 2^+-1000: at most 1.4 and 2.0 units in the
+// last place.  Zero, subnormal, infinite and NaN arguments take the library functions.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long e = (u >> 23) & 0xFF, mnt = u & 0x7FFFFF;
+  return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | ((e - 127 + 1023) << 52) | (mnt << 29)));
+}
+__device__ __forceinline__ double sqrt_fast(double T) {
+  const long long b = __double_as_longlong(T);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0 || e == 0x7FF) return sqrt(T);
+  const int k = (e - 1023) >> 1;
+  const long long mb = b - ((long long)(2 * k) << 52);  // T 2^-2k in [1, 4)
+  const float f = __uint_as_float((unsigned)((((mb >> 52) & 0x7FF) - 1023 + 127) << 23) | (unsigned)((mb >> 29) & 0x7FFFFF));
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+  const double s0 = f2d_exact(f * y), h0 = f2d_exact(0.5f * y);
+  const double s = __longlong_as_double(__double_as_longlong(s0) + ((long long)k << 52));
+  const double h = __longlong_as_double(__double_as_longlong(h0) - ((long long)k << 52));
+  double r = fma(-s, s, T);
+  const double s1 = fma(r, h, s);
+  r = fma(-s1, s1, T);
+  return fma(r, h, s1);
+}
+__device__ __forceinline__ double rcp_fast(double t) {
+  const long long b = __double_as_longlong(t);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e <= 1 || e >= 0x7FE) return 1.0 / t;
+  const int k = e - 1023;
+  const long long mb = b - ((long long)k << 52);  // |t| 2^-k in [1, 2)
+  const float f = __uint_as_float((unsigned)(127u << 23) | (unsigned)((mb >> 29) & 0x7FFFFF));
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+  double r = __longlong_as_double(__double_as_longlong(f2d_exact(y)) - ((long long)k << 52));
+  if (b < 0) r = -r;
+  const double q = fma(-t, r, 1.0);
+  return fma(r, fma(q, q, q), r);
+}
+__device__ __forceinline__ Refl<double> householder_fast(double rjj, double D, double eps) {
+  double t = fma(rjj, rjj, D) + eps;
+  double alpha = sqrt_fast(t + eps);
+  if (rjj > 0.0) alpha = -alpha;
+  t = fma(-alpha, rjj, t);
+  return {alpha, rjj - alpha, rcp_fast(t)};
+}
+
 // ---- phase 1: the reflector chain of one block ---------------------------------------
-// warp i (< kb) owns column j = j0 + i: applies the block's earlier reflectors as they are
-// published, then forms and publishes its own
+// the chain on four warps: warp w owns columns j0 + w (A) and j0 + w + 4 (B).  The owner of
+// the next pivot column applies the current pivot to that column and publishes its reflector
+// before it updates its other column, so the critical path meets no other chain warp's
+// FP64 work on its sub-partition.
 template <int MX, int PB>
-__device__ __forceinline__ bool chain(Smem<MX, PB>& S, int j0, int i, int lane, uint32_t par, int* status) {
+__device__ __forceinline__ void apply_piv(Smem<MX, PB>& S, double (&a)[PB / 32], const double (&x)[PB / 32],
+                                          double piv, double rt, int jp, int j, int lane) {
   constexpr int RPL = PB / 32;
-  const int j = j0 + i;
-  double a[RPL];
+  double d0 = 0.0, d1 = 0.0;
 #pragma unroll
-  for (int q = 0; q < RPL; ++q) a[q] = S.P[pix<MX>(lane + 32 * q, j)];
-  for (int jj = 0; jj < i; ++jj) {
+  for (int q = 0; q + 1 < RPL; q += 2) {
+    d0 = fma(x[q], a[q], d0);
+    d1 = fma(x[q + 1], a[q + 1], d1);
+  }
+  if constexpr (RPL % 2) d0 = fma(x[RPL - 1], a[RPL - 1], d0);
+  const double d = colk::warp_allsum<double>(d0 + d1);
+  const double r = S.R[rix<MX>(jp, j)];
+  const double c = fma(piv, r, d) * rt;
+  if (lane == 0) S.R[rix<MX>(jp, j)] = fma(-c, piv, r);
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) a[q] = fma(-c, x[q], a[q]);
+}
+template <int MX, int PB>
+__device__ __forceinline__ void publish_col(Smem<MX, PB>& S, double (&a)[PB / 32], int j, int lane) {
+  constexpr int RPL = PB / 32;
+  double n0 = 0.0, n1 = 0.0;
+#pragma unroll
+  for (int q = 0; q + 1 < RPL; q += 2) {
+    n0 = fma(a[q], a[q], n0);
+    n1 = fma(a[q + 1], a[q + 1], n1);
+  }
+  if constexpr (RPL % 2) n0 = fma(a[RPL - 1], a[RPL - 1], n0);
+  const double D = colk::warp_allsum<double>(n0 + n1);
+  const Refl<double> h = householder_fast(S.R[rix<MX>(j, j)], D, Tr<double>::eps());
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) S.P[pix<MX>(lane + 32 * q, j)] = a[q];
+  if (lane == 0) {
+    S.piv[j] = h.piv;
+    S.rt[j] = h.rt;
+    S.R[rix<MX>(j, j)] = h.alpha;
+  }
+  __syncwarp();
+  if (lane == 0) colk::mbar_arrive(reinterpret_cast<uint64_t*>(&S.bar[j]));
+  // the column's exponent (read by the tensor-core phases, after the block's barrier)
+  int em = 0;
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) em = max(em, efield(a[q]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+  if (lane == 0) S.colE[j] = em;
+}
+template <int MX, int PB>
+__device__ __forceinline__ bool chain(Smem<MX, PB>& S, int j0, int kb, int w, int lane, uint32_t par, int* status) {
+  constexpr int RPL = PB / 32;
+  const int ja = j0 + w, jb = j0 + w + 4;
+  const bool hasb = w + 4 < kb;
+  double a[RPL], b[RPL];
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    a[q] = S.P[pix<MX>(lane + 32 * q, ja)];
+    b[q] = hasb ? S.P[pix<MX>(lane + 32 * q, jb)] : 0.0;
+  }
+  if (w == 0) publish_col<MX, PB>(S, a, ja, lane);
+  const int last = hasb ? w + 4 : w;  // pivots needed: 0 .. last-1
+  for (int jj = 0; jj < last; ++jj) {
     const int jp = j0 + jj;
     if (!colk::mbar_wait(reinterpret_cast<uint64_t*>(&S.bar[jp]), par)) {
       if (lane == 0) {
@@ -156,45 +268,15 @@ __device__ __forceinline__ bool chain(Smem<MX, PB>& S, int j0, int i, int lane, 
 #pragma unroll
     for (int q = 0; q < RPL; ++q) x[q] = S.P[pix<MX>(lane + 32 * q, jp)];
     const double piv = S.piv[jp], rt = S.rt[jp];
-    double d0 = 0.0, d1 = 0.0;
-#pragma unroll
-    for (int q = 0; q + 1 < RPL; q += 2) {
-      d0 = fma(x[q], a[q], d0);
-      d1 = fma(x[q + 1], a[q + 1], d1);
+    if (jj < w) {
+      apply_piv<MX, PB>(S, a, x, piv, rt, jp, ja, lane);
+      if (jj == w - 1) publish_col<MX, PB>(S, a, ja, lane);
     }
-    if constexpr (RPL % 2) d0 = fma(x[RPL - 1], a[RPL - 1], d0);
-    const double d = colk::warp_allsum<double>(d0 + d1);
-    const double r = S.R[rix<MX>(jp, j)];
-    const double c = fma(piv, r, d) * rt;
-    if (lane == 0) S.R[rix<MX>(jp, j)] = fma(-c, piv, r);
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) a[q] = fma(-c, x[q], a[q]);
+    if (hasb) {
+      apply_piv<MX, PB>(S, b, x, piv, rt, jp, jb, lane);
+      if (jj == w + 3) publish_col<MX, PB>(S, b, jb, lane);
+    }
   }
-  double n0 = 0.0, n1 = 0.0;
-#pragma unroll
-  for (int q = 0; q + 1 < RPL; q += 2) {
-    n0 = fma(a[q], a[q], n0);
-    n1 = fma(a[q + 1], a[q + 1], n1);
-  }
-  if constexpr (RPL % 2) n0 = fma(a[RPL - 1], a[RPL - 1], n0);
-  const double D = colk::warp_allsum<double>(n0 + n1);
-  const Refl<double> h = householder(S.R[rix<MX>(j, j)], D, Tr<double>::eps());
-  int em = 0;
-#pragma unroll
-  for (int q = 0; q < RPL; ++q) {
-    S.P[pix<MX>(lane + 32 * q, j)] = a[q];
-    em = max(em, efield(a[q]));
-  }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
-  if (lane == 0) {
-    S.piv[j] = h.piv;
-    S.rt[j] = h.rt;
-    S.R[rix<MX>(j, j)] = h.alpha;
-    S.colE[j] = em;
-  }
-  __syncwarp();
-  if (lane == 0) colk::mbar_arrive(reinterpret_cast<uint64_t*>(&S.bar[j]));
   return true;
 }
 
@@ -291,6 +373,11 @@ __device__ __forceinline__ double level_value(const int (&s)[NLV], int e) {
   return pow2_split(fma((double)slo, 0x1p-24, (double)shi), e);
 }
 
+// an FP32 integer value |x| < 2^22 as an int: 1.5 2^23 + x has x in its low mantissa bits
+__device__ __forceinline__ int f2i_small(float x) {
+  return __float_as_int(__fadd_rn(x, 12582912.f)) - 0x4B400000;
+}
+
 // ---- phase 4: P_t -= X Z on the tensor cores ---------------------------------------------
 // warp w takes panel rows 16w .. 16w+15; K = 8, one mma per digit pair.  The sum runs over
 // the block's columns, whose scales may differ by any power of two, so the product is taken
@@ -347,9 +434,9 @@ __device__ __forceinline__ void prod2(Smem<MX, PB>& S, int j0, int m, int w, int
       if (c < m) {
         long long shi = 0, slo = 0;
 #pragma unroll
-        for (int l = 0; l < 4; ++l) shi = shi * 256 + __float2int_rn(acc[l][h]);
+        for (int l = 0; l < 4; ++l) shi = shi * 256 + f2i_small(acc[l][h]);
 #pragma unroll
-        for (int l = 4; l < NLV; ++l) slo = slo * 256 + __float2int_rn(acc[l][h]);
+        for (int l = 4; l < NLV; ++l) slo = slo * 256 + f2i_small(acc[l][h]);
         const long long T = shi * 65536 + (slo >> 8);
         const int e = ((h >> 1) ? eb : ea) + max(S.zE[c], 1) - 2084 - 16;
         const double y = scale2(__ll2double_rn(T), e);
@@ -444,7 +531,7 @@ k_tsqr_blk(const double* __restrict__ W, int64_t rows, int64_t ld, const int* __
     __syncthreads();
     for (int j0 = 0; j0 < m; j0 += KB) {
       const int kb = min(KB, m - j0);
-      if (w < kb) chain(S, j0, w, lane, par, status);
+      if (w < 4 && w < kb) chain(S, j0, kb, w, lane, par, status);
       __syncthreads();
       if (*reinterpret_cast<volatile int*>(&S.abort_flag)) {
         ok = false;
