@@ -15,7 +15,7 @@
 //      Schreiber & Van Loan 1989): with W = V^T C (W_ic = piv_i R_{j0+i,c} + x_i . P_c)
 //      and z_i = rt_i (W_i - sum_{i'<i} (x_i' . x_i) z_i') row by row,
 //          R_{j0+i,c} -= piv_i z_ic,   P_c -= X Z;
-//   3. the two products with the panel, X^T [X | P_trailing] (K = 128 rows) and X Z
+//   3. the two products with the panel, X^T [X | P_trailing] (K = PB rows) and X Z
 //      (K = 8), run on the tensor cores (mma.sync bf16, FP32 accumulation) with
 //      FP64-accurate Ozaki splitting (Ozaki, Ogita, Oishi, Rump 2012): every value
 //      becomes the 56-bit fixed-point magnitude of x relative to its group's largest
@@ -386,10 +386,9 @@ __device__ __forceinline__ int f2i_small(float x) {
 // with one exponent per column (zE, formed with the same scaling)
 __device__ __forceinline__ int ef1(double x) { return x != 0.0 ? max(efield(x), 1) : 0; }
 template <int MX, int PB>
-__device__ __forceinline__ void prod2(Smem<MX, PB>& S, int j0, int m, int w, int lane) {
-  if (w >= PB / 16) return;  // one 16-row m-tile per warp
+__device__ __forceinline__ void prod2(Smem<MX, PB>& S, int j0, int m, int tile, int ntb, int nte, int lane) {
   const int g = lane >> 2, t = lane & 3;
-  const int ra = 16 * w + g, rb = ra + 8;
+  const int ra = 16 * tile + g, rb = ra + 8;
   const int E0 = max(S.colE[j0 + 2 * t], 1), E1 = max(S.colE[j0 + 2 * t + 1], 1);
   const double xa0 = S.P[pix<MX>(ra, j0 + 2 * t)], xa1 = S.P[pix<MX>(ra, j0 + 2 * t + 1)];
   const double xb0 = S.P[pix<MX>(rb, j0 + 2 * t)], xb1 = S.P[pix<MX>(rb, j0 + 2 * t + 1)];
@@ -406,8 +405,9 @@ __device__ __forceinline__ void prod2(Smem<MX, PB>& S, int j0, int m, int w, int
   uint32_t Aa[NLV], Ab[NLV];
   digits2(xa0, ea + E0 - 1023, xa1, ea + E1 - 1023, Aa);
   digits2(xb0, eb + E0 - 1023, xb1, eb + E1 - 1023, Ab);
-  const int c0 = j0 + KB;
-  for (int cn0 = c0; cn0 < m; cn0 += 8) {
+  // n-tiles ntb .. nte-1 of the columns right of the block
+  const int cend = min(m, j0 + KB + 8 * nte);
+  for (int cn0 = j0 + KB + 8 * ntb; cn0 < cend; cn0 += 8) {
     const int cn = cn0 + g;  // B column of this lane
     uint32_t Bd[NLV];
     {
@@ -529,10 +529,9 @@ k_tsqr_blk(const double* __restrict__ W, int64_t rows, int64_t ld, const int* __
       }
     }
     __syncthreads();
-    for (int j0 = 0; j0 < m; j0 += KB) {
-      const int kb = min(KB, m - j0);
-      if (w < 4 && w < kb) chain(S, j0, kb, w, lane, par, status);
-      __syncthreads();
+    if (w < 4 && w < min(KB, m)) chain(S, 0, min(KB, m), w, lane, par, status);
+    __syncthreads();
+    for (int j0 = 0;; j0 += KB) {
       if (*reinterpret_cast<volatile int*>(&S.abort_flag)) {
         ok = false;
         break;
@@ -575,7 +574,17 @@ k_tsqr_blk(const double* __restrict__ W, int64_t rows, int64_t ld, const int* __
         S.colE[c] = 0;  // recomputed from the updated panel values
       }
       __syncthreads();
-      prod2(S, j0, m, w, lane);
+      // P -= X Z: first the next block's columns (one n-tile, a 16-row m-tile per warp),
+      // then the next block's reflector chain (warps 0-3) runs beside the rest of the
+      // update (warps 4-7; disjoint columns of P, colE and R)
+      if (w < PB / 16) prod2(S, j0, m, w, 0, 1, lane);
+      __syncthreads();
+      const int j1 = j0 + KB, kb1 = min(KB, m - j1);
+      if (w < 4) {
+        if (w < kb1) chain(S, j1, kb1, w, lane, par, status);
+      } else {
+        for (int tile = w - 4; tile < PB / 16; tile += 4) prod2(S, j0, m, tile, 1, MX / 8, lane);
+      }
       __syncthreads();
     }
   }
