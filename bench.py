@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--serve-seconds", type=float, default=4.0)
     p.add_argument("--case", default="", help="one building block for profiling instead of the bench: "
-                   "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix), tsqr64:ROWS:M (native FP64), "
+                   "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix), tsqr64:ROWS:M (native FP64), ttsvd32:N:D:RMAX (FP32 form), "
                    "tsmm:ROWS:M:K (W V(:, 0:K) of a uniform FP64 W) or svd:M (small SVD of a "
                    "uniform upper-triangular R) or ttsvd:N:D:RMAX:ARITH (a whole TT-SVD of a "
                    "uniform N^D FP64 tensor, ARITH f64 or df), each optionally followed by "
@@ -288,6 +288,12 @@ def run_case(spec: str) -> int:
         n, d, r, ar = int(parts[1]), int(parts[2]), int(parts[3]), parts[4]
         X = api.gen_uniform(n ** d, 3, torch.float64)
         plan = api.TTSVDPlan([n] * d, r, 0.0, torch.float64, ar)
+        call = lambda: plan.run(X)
+    elif parts[0] == "ttsvd32":
+        # ttsvd32:N:D:RMAX -- the FP32 form (FP32 storage and panels) of a uniform N^D tensor
+        n, d, r = int(parts[1]), int(parts[2]), int(parts[3])
+        X = api.gen_uniform(n ** d, 3, torch.float32)
+        plan = api.TTSVDPlan([n] * d, r, 0.0, torch.float32, "df")
         call = lambda: plan.run(X)
     elif parts[0] == "svd":
         m = int(parts[1])
