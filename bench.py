@@ -67,6 +67,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip sweep, FP32 form, e2e, CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--serve-seconds", type=float, default=4.0)
+    p.add_argument("--serve-only", action="store_true", help="only the serving leg (both admission orders)")
     p.add_argument("--case", default="", help="one building block for profiling instead of the bench: "
                    "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix), tsqr64:ROWS:M (native FP64), ttsvd32:N:D:RMAX (FP32 form), "
                    "tsmm:ROWS:M:K (W V(:, 0:K) of a uniform FP64 W) or svd:M (small SVD of a "
@@ -450,6 +451,17 @@ def main():
         return run_case(args.case)
     if args.alg5:
         return run_alg5(args)
+    if args.serve_only:
+        import torch
+
+        import __graft_entry__ as G
+        from paper_2102_00104_gb300 import api, capi
+        G.build()
+        capi.lib()
+        out = {"serve": bench_serve(api, capi, torch, args.seed, args.serve_seconds, capi.TT_SERVE_SHORTEST, 10.0),
+               "serve_fifo": bench_serve(api, capi, torch, args.seed, args.serve_seconds, capi.TT_SERVE_FIFO, 0.0)}
+        print(json.dumps(out), flush=True)
+        return 0
 
     import torch
     import torch.distributed as dist
@@ -640,7 +652,9 @@ def run_extras(args, api, capi, torch, X, plan, dims, nbar, in_bytes, hbm_peak, 
     out["two_sided_df"] = two
     out["fp32_form"] = bench_fp32_form(args, api, torch, X, dims, nbar, stream, hbm_peak)
     out["batched"] = bench_batched(api, capi, torch, stream, args.seed)
-    out["serve"] = bench_serve(api, capi, torch, args.seed, args.serve_seconds)
+    # shortest estimated work first (a request waiting 10 s goes first), then FIFO for comparison
+    out["serve"] = bench_serve(api, capi, torch, args.seed, args.serve_seconds, capi.TT_SERVE_SHORTEST, 10.0)
+    out["serve_fifo"] = bench_serve(api, capi, torch, args.seed, args.serve_seconds, capi.TT_SERVE_FIFO, 0.0)
     # oracle on the host cores
     gbs, sec, cores, sample = cpu_oracle_rate(args.n, args.rmax, args.cpu_seconds, args.seed)
     out["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
@@ -765,13 +779,14 @@ def bench_batched(api, capi, torch, stream, seed, count=256):
 SERVE_SLOTS = 64
 
 
-def bench_serve(api, capi, torch, seed, seconds):
+def bench_serve(api, capi, torch, seed, seconds, policy, max_wait_s):
     """The serving configuration: Poisson arrivals at 200 req/s for `seconds`; requests with
     d in 6..14, n_j from {2,3,4,8} and 2^14..2^28 entries (log-uniform), 50/50 FP64/FP32;
     half use r_max in {4,8,16,32} on uniform inputs, half tol in {1e-2,1e-4} with an r_max
     cap of 64 on planted-rank inputs (ranks 4..32, 1e-3 relative noise).  Inputs come from a
     pool of 48 device-resident tensors made before the arrivals (not timed); the server
-    admits requests under a 150 GB budget with SERVE_SLOTS slots."""
+    admits requests under a 150 GB budget with SERVE_SLOTS slots, in the given admission
+    order (TT_SERVE_SHORTEST with its aging bound, or TT_SERVE_FIFO)."""
     import numpy as np
     from paper_2102_00104_gb300.inputs import planted_tt_device
     rng = np.random.default_rng(seed + 5)
@@ -788,7 +803,8 @@ def bench_serve(api, capi, torch, seed, seconds):
         pool.append((dims, X, spec))
     torch.cuda.synchronize()
     torch.cuda.empty_cache()  # the server's arena is one allocation outside torch's cache
-    srv = capi.tt_serve_create(150 << 30, max_inflight=SERVE_SLOTS, arena_bytes=96 << 30)
+    srv = capi.tt_serve_create(150 << 30, max_inflight=SERVE_SLOTS, arena_bytes=96 << 30, policy=policy,
+                               max_wait_s=max_wait_s)
     n_req = int(200 * seconds)
     gaps = rng.exponential(1.0 / 200.0, size=n_req)
     picks = rng.integers(0, len(pool), size=n_req)
@@ -828,7 +844,9 @@ def bench_serve(api, capi, torch, seed, seconds):
             "sizes": "2^14..2^28 entries (log-uniform), d 6..14, n_j in {2,3,4,8}, 50/50 FP64/FP32; "
                      "r_max in {4,8,16,32} or tol in {1e-2,1e-4} (r_max cap 64); pool of 48 "
                      f"device-resident inputs, largest {sizes[-1]} entries",
-            "budget_bytes": 150 << 30, "slots": SERVE_SLOTS, "arena_bytes": 96 << 30}
+            "budget_bytes": 150 << 30, "slots": SERVE_SLOTS, "arena_bytes": 96 << 30,
+            "admission": ("shortest estimated work first, oldest first after %.0f s" % max_wait_s
+                          if policy == capi.TT_SERVE_SHORTEST else "FIFO")}
 
 
 if __name__ == "__main__":

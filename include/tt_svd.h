@@ -283,7 +283,16 @@ typedef struct {
   int max_inflight;         /* slots (concurrent requests on the device), >= 1 */
   size_t arena_bytes;       /* workspace arena; 0 = a quarter of the budget */
   double timeout_s;         /* limit for a blocking tt_serve_poll (0 = 60 s) */
+  int policy;               /* admission order: TT_SERVE_FIFO (0) or TT_SERVE_SHORTEST (1) */
+  double max_wait_s;        /* TT_SERVE_SHORTEST: a request queued this long is admitted
+                               next regardless of its size (0 = 1 s) */
 } tt_serve_opts;
+/* Admission order.  FIFO: in arrival order.  SHORTEST: the queued request with the least
+ * estimated device work (the plan's TSQR, small-SVD and W V_r costs) first, except that
+ * the oldest request goes first once it has waited max_wait_s (no request waits
+ * indefinitely while smaller ones keep arriving).  Both stop at the first request the
+ * budget or the arena cannot take yet. */
+enum { TT_SERVE_FIFO = 0, TT_SERVE_SHORTEST = 1 };
 typedef struct {
   tt_status status;         /* TT_OK, a launch error, TT_ENUMERIC, TT_ECANCELLED ... */
   double t_submit, t_start, t_done;   /* steady-clock seconds: queued, admitted, seen done */

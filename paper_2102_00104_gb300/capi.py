@@ -44,7 +44,8 @@ class tt_job(C.Structure):
 
 
 class tt_serve_opts(C.Structure):
-    _fields_ = [("max_inflight", C.c_int), ("arena_bytes", C.c_size_t), ("timeout_s", C.c_double)]
+    _fields_ = [("max_inflight", C.c_int), ("arena_bytes", C.c_size_t), ("timeout_s", C.c_double),
+                ("policy", C.c_int), ("max_wait_s", C.c_double)]
 
 
 class tt_job_result(C.Structure):
@@ -277,9 +278,13 @@ def tt_svd_batched(jobs, work_ptr, work_bytes, stream=0):
     check(lib().tt_svd_batched(len(jobs), arr, work_ptr, work_bytes, stream), "tt_svd_batched")
 
 
-def tt_serve_create(budget_bytes, max_inflight=8, arena_bytes=0, timeout_s=60.0):
+TT_SERVE_FIFO, TT_SERVE_SHORTEST = 0, 1
+
+
+def tt_serve_create(budget_bytes, max_inflight=8, arena_bytes=0, timeout_s=60.0, policy=TT_SERVE_FIFO,
+                    max_wait_s=0.0):
     srv = C.c_void_p(0)
-    opts = tt_serve_opts(max_inflight, arena_bytes, timeout_s)
+    opts = tt_serve_opts(max_inflight, arena_bytes, timeout_s, policy, max_wait_s)
     check(lib().tt_serve_create(budget_bytes, C.byref(opts), C.byref(srv)), "tt_serve_create")
     return srv
 

@@ -163,9 +163,12 @@ struct tt_server {
     tt_job_result res{};
     bool done = false;
     cudaEvent_t ready = nullptr;  // recorded on the submitter's stream: inputs and outputs ready
+    double cost = 0.0;            // estimated device seconds (job_cost_estimate)
   };
   size_t budget = 0, arena_bytes = 0, accounted = 0;
   double timeout_s = 60.0;
+  int policy = TT_SERVE_FIFO;
+  double max_wait_s = 1.0;
   char* arena = nullptr;
   std::vector<std::pair<size_t, size_t>> free_list;  // (offset, size), sorted by offset
   std::vector<cudaStream_t> slot_stream;
@@ -241,11 +244,18 @@ struct tt_server {
       for (size_t k = 0; k < slot_ticket.size(); ++k)
         if (!slot_ticket[k]) { slot = (int)k; break; }
       if (slot < 0) break;
-      Req& r = reqs[queue.front()];
-      if (accounted + r.acct > budget) break;   // FIFO: wait for memory to free up
+      // the next request: the head of the queue, or (SHORTEST) the least estimated work
+      // unless the head has waited max_wait_s
+      size_t pick = 0;
+      if (policy == TT_SERVE_SHORTEST && now_s() - reqs[queue.front()].res.t_submit < max_wait_s) {
+        for (size_t q = 1; q < queue.size(); ++q)
+          if (reqs[queue[q]].cost < reqs[queue[pick]].cost) pick = q;
+      }
+      Req& r = reqs[queue[pick]];
+      if (accounted + r.acct > budget) break;   // wait for memory to free up
       size_t off = 0;
       if (!arena_alloc(r.ws, &off)) break;
-      queue.pop_front();
+      queue.erase(queue.begin() + (std::ptrdiff_t)pick);
       r.arena_off = off;
       r.slot = slot;
       r.res.t_start = now_s();
@@ -298,6 +308,12 @@ tt_status tt_serve_create(size_t hbm_budget_bytes, const tt_serve_opts* opts, tt
   s->arena_bytes = opts && opts->arena_bytes ? opts->arena_bytes : hbm_budget_bytes / 4;
   s->arena_bytes = (s->arena_bytes + 255) & ~(size_t)255;
   s->timeout_s = opts && opts->timeout_s > 0 ? opts->timeout_s : 60.0;
+  if (opts && opts->policy != TT_SERVE_FIFO && opts->policy != TT_SERVE_SHORTEST) {
+    delete s;
+    return TT_EINVAL;
+  }
+  s->policy = opts ? opts->policy : TT_SERVE_FIFO;
+  s->max_wait_s = opts && opts->max_wait_s > 0 ? opts->max_wait_s : 1.0;
   if (cudaGetDevice(&s->device) != cudaSuccess ||
       cudaMalloc(&s->arena, s->arena_bytes) != cudaSuccess) {
     delete s;
@@ -351,6 +367,7 @@ tt_status tt_serve_submit(tt_server* s, const tt_job* job, void* ready_stream, u
   r.acct = acct;
   r.res.status = TT_OK;
   r.res.t_submit = now_s();
+  r.cost = job_cost_estimate(job->d, job->n, job->r_max, job->tol, (int)job->dtype);
   s->reqs[r.ticket] = r;
   s->queue.push_back(r.ticket);
   *ticket = r.ticket;

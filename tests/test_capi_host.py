@@ -149,6 +149,8 @@ def test_batched_and_serve_argument_checks(lib):
     assert lib.tt_svd_batched(1, arr, C.c_void_p(4097), 1 << 30, None) == capi.TT_EINVAL
     srv = C.c_void_p(0)
     assert lib.tt_serve_create(0, None, C.byref(srv)) == capi.TT_EINVAL
+    bad_policy = capi.tt_serve_opts(4, 0, 1.0, 7, 0.0)  # rejected before any CUDA call
+    assert lib.tt_serve_create(1 << 30, C.byref(bad_policy), C.byref(srv)) == capi.TT_EINVAL
     res = capi.tt_job_result()
     assert lib.tt_serve_poll(None, 1, 0, C.byref(res)) == capi.TT_EINVAL
     assert lib.tt_serve_destroy(None) == capi.TT_EINVAL

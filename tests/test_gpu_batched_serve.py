@@ -250,3 +250,32 @@ def test_serve_admission_under_budget_and_cancel():
     assert capi.lib().tt_serve_destroy(srv) == capi.TT_OK
     assert time.time() - t0 < 30
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("policy,max_wait,small_first", [(capi.TT_SERVE_SHORTEST, 30.0, True),
+                                                         (capi.TT_SERVE_FIFO, 0.0, False),
+                                                         (capi.TT_SERVE_SHORTEST, 1e-6, False)])
+def test_serve_admission_order(policy, max_wait, small_first):
+    # one slot: a long request holds it while a large and three small requests queue.
+    # SHORTEST admits the small ones before the large one; FIFO, or SHORTEST once the
+    # large one has waited max_wait_s, admits in arrival order
+    srv = capi.tt_serve_create(32 << 30, max_inflight=1, policy=policy, max_wait_s=max_wait)
+    try:
+        blocker = api.Job(api.gen_uniform(8 ** 8, 1, torch.float64), (8,) * 8, 10)
+        big = api.Job(api.gen_uniform(8 ** 7, 2, torch.float64), (8,) * 7, 10)
+        small = [api.Job(api.gen_uniform(4 ** 6, 3 + k, torch.float64), (4,) * 6, 4) for k in range(3)]
+        torch.cuda.synchronize()
+        tickets = [api.serve_submit(srv, j) for j in [blocker, big] + small]
+        res = []
+        for t in tickets:
+            code, r = capi.tt_serve_poll(srv, t, wait=True)
+            assert code == capi.TT_OK and r.status == capi.TT_OK
+            res.append(r)
+        t_big = res[1].t_start
+        t_small = [r.t_start for r in res[2:]]
+        if small_first:
+            assert all(t < t_big for t in t_small), (t_big, t_small)
+        else:
+            assert all(t > t_big for t in t_small), (t_big, t_small)
+    finally:
+        capi.tt_serve_destroy(srv)
