@@ -551,7 +551,7 @@ def main():
         "two_read_roofline": {"ms": two_read_ms, "frac": two_read_ms / ms, "hbm_gbs": hbm_peak, "source": peak_src},
         "roofline": roof,
         "alu_peaks_tflops": alu_peaks,
-        "per_kernel": per_kernel[:8],
+        "per_kernel": per_kernel,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
