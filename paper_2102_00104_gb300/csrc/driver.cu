@@ -132,7 +132,18 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
   int64_t warps_cap;
   int cta_pr = 0, cta_nw = 0, cta_per_sm = 1;
   int cta_kind = 3;
-  int cta_cfg = m_max > 16 ? tsqr_col_pick(m_max, in, comp, out, &cta_pr, &cta_nw, &cta_per_sm) : -1;
+  int cta_cfg = -1;
+  // native FP64, 16 < m <= 512: the blocked kernel ("tsqr.blk64" up to m = 80, "tsqr.blkw" above)
+  if (in == Fmt::F64 && comp == Fmt::F64 && out == Fmt::F64 && m_max > 16 && m_max <= 512 &&
+      tune_get("tsqr.blk64", 1) != 0 && (m_max <= 80 || tune_get("tsqr.blkw", 1) != 0) &&
+      (m_max <= 64 || tune_get("tsqr.blk80", 1) != 0)) {
+    cta_kind = 6;
+    cta_cfg = 0;
+    cta_pr = tsqr_blk_rows(m_max);
+    cta_nw = 8;
+    cta_per_sm = tsqr_blk_per_sm(m_max);
+  }
+  if (cta_cfg < 0 && m_max > 16) cta_cfg = tsqr_col_pick(m_max, in, comp, out, &cta_pr, &cta_nw, &cta_per_sm);
   if (cta_cfg < 0) {
     cta_kind = 4;
     cta_cfg = tsqr_cols_pick(m_max, in, comp, out, &cta_pr, &cta_nw, &cta_per_sm);
@@ -148,7 +159,8 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
     L.maxm = m_max;
     L.pr = cta_pr;
     L.nw = cta_nw;
-    L.smem = cta_kind == 3   ? tsqr_col_smem(m_max, comp, cta_cfg)
+    L.smem = cta_kind == 6   ? tsqr_blk_smem(m_max)
+             : cta_kind == 3 ? tsqr_col_smem(m_max, comp, cta_cfg)
              : cta_kind == 4 ? tsqr_cols_smem(m_max, cta_cfg)
                              : tsqr_cta_smem(m_max, comp, cta_cfg);
     L.panels = (rows + L.pr - 1) / L.pr;

@@ -83,7 +83,8 @@ struct TsqrLevel {
                      // 2 = CTA-cooperative (register panels, R in shared memory),
                      // 3 = column-owned CTA kernel (one barrier per column, look-ahead),
                      // 4 = column-owned with the panel in shared memory (wide m),
-                     // 5 = pairwise merge of the stacked triangles (upper levels only)
+                     // 5 = pairwise merge of the stacked triangles (upper levels only),
+                     // 6 = blocked native-FP64 kernel (tensor-core trailing updates)
   int cfg;           // kind 2: layout id (see tsqr_cta.cu); kind 3: see tsqr_col.cu
   int maxm;          // narrow: 4/8/16 ; wide: 32*chunks (template bound)
   int mmax;          // worst-case m of this level (<= maxm)
@@ -117,14 +118,15 @@ int tsqr_col_pick(int m_max, Fmt in, Fmt comp, Fmt out, int* pr, int* nw, int* p
 size_t tsqr_col_smem(int m_max, Fmt comp, int id);
 cudaError_t launch_tsqr_col(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
                             void* Rout, int64_t ldR, int* status, cudaStream_t s);
-// kind 3, layout id 15: the blocked native-FP64 kernel (compact-WY blocks of 8 reflectors,
-// trailing updates on the tensor cores; m <= 64 with 128-row panels, m <= 80 with 96-row
-// panels, 2 CTAs per SM)
-constexpr int kTsqrBlkId = 15;
+// kind 6: the blocked native-FP64 kernel (compact-WY blocks of 8 reflectors, trailing
+// updates on the tensor cores), 16 < m <= 512: rows per panel, CTAs per SM, shared memory
+// and (m > 80: R in a global slice per CTA) scratch bytes per layout
 size_t tsqr_blk_smem(int m_max);
 int tsqr_blk_rows(int m_max);
+int tsqr_blk_per_sm(int m_max);
+size_t tsqr_blk_scratch(int m_max, int64_t ctas);
 cudaError_t launch_tsqr_blk(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev,
-                            void* Rout, int64_t ldR, int* status, cudaStream_t s);
+                            void* Rout, int64_t ldR, void* Rscr, int* status, cudaStream_t s);
 // kind 4 (shared-memory panels, R in an L2-resident global slice per CTA): rows per lane or -1
 int tsqr_cols_pick(int m_max, Fmt in, Fmt comp, Fmt out, int* pr, int* nw, int* per_sm);
 size_t tsqr_cols_smem(int m_max, int prl);

@@ -71,6 +71,7 @@ size_t tsqr_wide_scratch_bytes(const TsqrLevel& L) {
   if (L.kind == 2) return tsqr_cta_scratch(L.mmax, L.comp, L.cfg, L.ctas);
   if (L.kind == 4) return tsqr_cols_scratch(L.mmax, L.ctas);
   if (L.kind == 5) return tsqr_merge_scratch(L.mmax, L.comp, L.ctas);
+  if (L.kind == 6) return tsqr_blk_scratch(L.mmax, L.ctas);
   if (L.kind != 1) return 0;  // kinds 0 and 3 keep R in registers / shared memory
   return (size_t)L.warps * L.mmax * L.mmax * fmt_bytes(L.comp);
 }
@@ -81,6 +82,7 @@ cudaError_t launch_tsqr_level(const TsqrLevel& L, const void* W, int64_t ld, con
   if (L.kind == 3) return launch_tsqr_col(L, W, ld, m_dev, Rout, ldR, status, s);
   if (L.kind == 4) return launch_tsqr_cols(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
   if (L.kind == 5) return launch_tsqr_merge(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+  if (L.kind == 6) return launch_tsqr_blk(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
   if (L.in == Fmt::F64 && L.comp == Fmt::DF && L.out == Fmt::DF)
     return run_typed<df, double, df>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
   if (L.in == Fmt::DF && L.comp == Fmt::DF && L.out == Fmt::DF)

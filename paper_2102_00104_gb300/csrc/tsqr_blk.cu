@@ -54,6 +54,8 @@ __device__ __forceinline__ int rix(int i, int c) { return i * MX - (i * (i - 1))
 
 template <int MX, int PB>
 struct Smem {
+  static constexpr int kMX = MX, kPB = PB;
+  static constexpr bool kWide = false;
   double P[PB * MX];
   double R[MX * (MX + 1) / 2];
   double Z[KB * MX];   // W_ic, then z_ic in place (c = panel column)
@@ -67,8 +69,35 @@ struct Smem {
   int abort_flag;
 };
 
+// The wide layouts (80 < m <= 512): R is a packed triangle per CTA in global memory (an
+// L2-resident slice of the level's scratch); the 8 rows of the block being factored are
+// staged in shared memory (Rb, row i at i * MX), read at the block's start and written
+// back at its end.  The panel product's level sums stay in each warp (a warp takes whole
+// 16-row tiles over the panel's rows), so no shared level-sum table is needed.
 template <int MX, int PB>
-__host__ __device__ constexpr size_t smem_bytes() { return sizeof(Smem<MX, PB>); }
+struct SmemW {
+  static constexpr int kMX = MX, kPB = PB;
+  static constexpr bool kWide = true;
+  double P[PB * MX];
+  double Rb[KB * MX];
+  double Z[KB * MX];
+  double G[KB * KB];
+  double piv[MX];
+  double rt[MX];
+  int colE[MX];
+  int zE[MX];
+  unsigned long long bar[MX];
+  int abort_flag;
+};
+
+// R_{i,c} of the CTA's triangle for a row i of the current block (first row j0)
+template <int MX, int PB>
+__device__ __forceinline__ double& Rref(Smem<MX, PB>& S, int i, int c, int) { return S.R[rix<MX>(i, c)]; }
+template <int MX, int PB>
+__device__ __forceinline__ double& Rref(SmemW<MX, PB>& S, int i, int c, int j0) { return S.Rb[(i - j0) * MX + c]; }
+
+template <int MX, int PB>
+__host__ __device__ constexpr size_t smem_bytes() { return MX > 80 ? sizeof(SmemW<MX, PB>) : sizeof(Smem<MX, PB>); }
 
 // ---- FP64-accurate digits ------------------------------------------------------------
 // u = floor(|x| 2^(1078 - em)) < 2^56 for |x| < 2^(em - 1022), as (hi: 24 bits, lo: 32 bits)
@@ -195,10 +224,10 @@ __device__ __forceinline__ Refl<double> householder_fast(double rjj, double D, d
 // the next pivot column applies the current pivot to that column and publishes its reflector
 // before it updates its other column, so the critical path meets no other chain warp's
 // FP64 work on its sub-partition.
-template <int MX, int PB>
-__device__ __forceinline__ void apply_piv(Smem<MX, PB>& S, double (&a)[PB / 32], const double (&x)[PB / 32],
-                                          double piv, double rt, int jp, int j, int lane) {
-  constexpr int RPL = PB / 32;
+template <class SM>
+__device__ __forceinline__ void apply_piv(SM& S, double (&a)[SM::kPB / 32], const double (&x)[SM::kPB / 32],
+                                          double piv, double rt, int jp, int j, int j0, int lane) {
+  constexpr int RPL = SM::kPB / 32;
   double d0 = 0.0, d1 = 0.0;
 #pragma unroll
   for (int q = 0; q + 1 < RPL; q += 2) {
@@ -207,15 +236,16 @@ __device__ __forceinline__ void apply_piv(Smem<MX, PB>& S, double (&a)[PB / 32],
   }
   if constexpr (RPL % 2) d0 = fma(x[RPL - 1], a[RPL - 1], d0);
   const double d = colk::warp_allsum<double>(d0 + d1);
-  const double r = S.R[rix<MX>(jp, j)];
+  double& rr = Rref(S, jp, j, j0);
+  const double r = rr;
   const double c = fma(piv, r, d) * rt;
-  if (lane == 0) S.R[rix<MX>(jp, j)] = fma(-c, piv, r);
+  if (lane == 0) rr = fma(-c, piv, r);
 #pragma unroll
   for (int q = 0; q < RPL; ++q) a[q] = fma(-c, x[q], a[q]);
 }
-template <int MX, int PB>
-__device__ __forceinline__ void publish_col(Smem<MX, PB>& S, double (&a)[PB / 32], int j, int lane) {
-  constexpr int RPL = PB / 32;
+template <class SM>
+__device__ __forceinline__ void publish_col(SM& S, double (&a)[SM::kPB / 32], int j, int j0, int lane) {
+  constexpr int RPL = SM::kPB / 32, MX = SM::kMX;
   double n0 = 0.0, n1 = 0.0;
 #pragma unroll
   for (int q = 0; q + 1 < RPL; q += 2) {
@@ -224,13 +254,14 @@ __device__ __forceinline__ void publish_col(Smem<MX, PB>& S, double (&a)[PB / 32
   }
   if constexpr (RPL % 2) n0 = fma(a[RPL - 1], a[RPL - 1], n0);
   const double D = colk::warp_allsum<double>(n0 + n1);
-  const Refl<double> h = householder_fast(S.R[rix<MX>(j, j)], D, Tr<double>::eps());
+  double& rjj = Rref(S, j, j, j0);
+  const Refl<double> h = householder_fast(rjj, D, Tr<double>::eps());
 #pragma unroll
   for (int q = 0; q < RPL; ++q) S.P[pix<MX>(lane + 32 * q, j)] = a[q];
   if (lane == 0) {
     S.piv[j] = h.piv;
     S.rt[j] = h.rt;
-    S.R[rix<MX>(j, j)] = h.alpha;
+    rjj = h.alpha;
   }
   __syncwarp();
   if (lane == 0) colk::mbar_arrive(reinterpret_cast<uint64_t*>(&S.bar[j]));
@@ -242,9 +273,9 @@ __device__ __forceinline__ void publish_col(Smem<MX, PB>& S, double (&a)[PB / 32
   for (int o = 16; o; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
   if (lane == 0) S.colE[j] = em;
 }
-template <int MX, int PB>
-__device__ __forceinline__ bool chain(Smem<MX, PB>& S, int j0, int kb, int w, int lane, uint32_t par, int* status) {
-  constexpr int RPL = PB / 32;
+template <class SM>
+__device__ __forceinline__ bool chain(SM& S, int j0, int kb, int w, int lane, uint32_t par, int* status) {
+  constexpr int RPL = SM::kPB / 32, MX = SM::kMX;
   const int ja = j0 + w, jb = j0 + w + 4;
   const bool hasb = w + 4 < kb;
   double a[RPL], b[RPL];
@@ -253,7 +284,7 @@ __device__ __forceinline__ bool chain(Smem<MX, PB>& S, int j0, int kb, int w, in
     a[q] = S.P[pix<MX>(lane + 32 * q, ja)];
     b[q] = hasb ? S.P[pix<MX>(lane + 32 * q, jb)] : 0.0;
   }
-  if (w == 0) publish_col<MX, PB>(S, a, ja, lane);
+  if (w == 0) publish_col(S, a, ja, j0, lane);
   const int last = hasb ? w + 4 : w;  // pivots needed: 0 .. last-1
   for (int jj = 0; jj < last; ++jj) {
     const int jp = j0 + jj;
@@ -269,12 +300,12 @@ __device__ __forceinline__ bool chain(Smem<MX, PB>& S, int j0, int kb, int w, in
     for (int q = 0; q < RPL; ++q) x[q] = S.P[pix<MX>(lane + 32 * q, jp)];
     const double piv = S.piv[jp], rt = S.rt[jp];
     if (jj < w) {
-      apply_piv<MX, PB>(S, a, x, piv, rt, jp, ja, lane);
-      if (jj == w - 1) publish_col<MX, PB>(S, a, ja, lane);
+      apply_piv(S, a, x, piv, rt, jp, ja, j0, lane);
+      if (jj == w - 1) publish_col(S, a, ja, j0, lane);
     }
     if (hasb) {
-      apply_piv<MX, PB>(S, b, x, piv, rt, jp, jb, lane);
-      if (jj == w + 3) publish_col<MX, PB>(S, b, jb, lane);
+      apply_piv(S, b, x, piv, rt, jp, jb, j0, lane);
+      if (jj == w + 3) publish_col(S, b, jb, j0, lane);
     }
   }
   return true;
@@ -385,8 +416,9 @@ __device__ __forceinline__ int f2i_small(float x) {
 // scalings, folded into the digit exponents): A = X D^-1 with one exponent per row, B = D Z
 // with one exponent per column (zE, formed with the same scaling)
 __device__ __forceinline__ int ef1(double x) { return x != 0.0 ? max(efield(x), 1) : 0; }
-template <int MX, int PB>
-__device__ __forceinline__ void prod2(Smem<MX, PB>& S, int j0, int m, int tile, int ntb, int nte, int lane) {
+template <class SM>
+__device__ __forceinline__ void prod2(SM& S, int j0, int m, int tile, int ntb, int nte, int lane) {
+  constexpr int MX = SM::kMX;
   const int g = lane >> 2, t = lane & 3;
   const int ra = 16 * tile + g, rb = ra + 8;
   const int E0 = max(S.colE[j0 + 2 * t], 1), E1 = max(S.colE[j0 + 2 * t + 1], 1);
@@ -460,6 +492,90 @@ __device__ __forceinline__ void prod2(Smem<MX, PB>& S, int j0, int m, int tile, 
   }
 }
 
+
+// ---- the wide layouts' panel product: a warp takes whole 16-row tiles of A over all PB
+// rows (PB / 16 k-steps; the level sums of two k-steps stay below 2^24 in FP32 and are
+// emptied into integers), and forms G and W from its own sums
+template <int MX, int PB>
+__device__ __forceinline__ void prod1w(SmemW<MX, PB>& S, int j0, int m, int w, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  const int M1 = m - j0;
+  const int mt = (M1 + 15) >> 4;
+  const int cb = j0 + g;
+  const int emb = max(S.colE[cb], 1);
+  for (int tile = w; tile < mt; tile += NW) {
+    const int rho0 = 16 * tile + g, rho1 = rho0 + 8;
+    const bool in0 = rho0 < M1, in1 = rho1 < M1;
+    const int ca0 = j0 + rho0, ca1 = j0 + rho1;
+    const int ema0 = in0 ? max(S.colE[ca0], 1) : 1, ema1 = in1 ? max(S.colE[ca1], 1) : 1;
+    int ia[NLV][4];
+    float acc[NLV][4];
+#pragma unroll
+    for (int l = 0; l < NLV; ++l)
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        ia[l][h] = 0;
+        acc[l][h] = 0.f;
+      }
+#pragma unroll 1
+    for (int kk = 0; kk < PB / 16; ++kk) {
+      const int r0 = 16 * kk + 2 * t;
+      uint32_t A[NLV][4], B[NLV][2];
+      {
+        uint32_t d[NLV];
+        const double v00 = in0 ? S.P[pix<MX>(r0, ca0)] : 0.0, v01 = in0 ? S.P[pix<MX>(r0 + 1, ca0)] : 0.0;
+        const double v10 = in1 ? S.P[pix<MX>(r0, ca1)] : 0.0, v11 = in1 ? S.P[pix<MX>(r0 + 1, ca1)] : 0.0;
+        const double v20 = in0 ? S.P[pix<MX>(r0 + 8, ca0)] : 0.0, v21 = in0 ? S.P[pix<MX>(r0 + 9, ca0)] : 0.0;
+        const double v30 = in1 ? S.P[pix<MX>(r0 + 8, ca1)] : 0.0, v31 = in1 ? S.P[pix<MX>(r0 + 9, ca1)] : 0.0;
+        digits2(v00, ema0, v01, ema0, d);
+#pragma unroll
+        for (int a = 0; a < NLV; ++a) A[a][0] = d[a];
+        digits2(v10, ema1, v11, ema1, d);
+#pragma unroll
+        for (int a = 0; a < NLV; ++a) A[a][1] = d[a];
+        digits2(v20, ema0, v21, ema0, d);
+#pragma unroll
+        for (int a = 0; a < NLV; ++a) A[a][2] = d[a];
+        digits2(v30, ema1, v31, ema1, d);
+#pragma unroll
+        for (int a = 0; a < NLV; ++a) A[a][3] = d[a];
+        digits2(S.P[pix<MX>(r0, cb)], emb, S.P[pix<MX>(r0 + 1, cb)], emb, d);
+#pragma unroll
+        for (int b = 0; b < NLV; ++b) B[b][0] = d[b];
+        digits2(S.P[pix<MX>(r0 + 8, cb)], emb, S.P[pix<MX>(r0 + 9, cb)], emb, d);
+#pragma unroll
+        for (int b = 0; b < NLV; ++b) B[b][1] = d[b];
+      }
+#pragma unroll
+      for (int a = 0; a < NLV; ++a)
+#pragma unroll
+        for (int b = 0; a + b < NLV; ++b) mma16816(acc[a + b], A[a], B[b][0], B[b][1]);
+      if (kk & 1) {
+#pragma unroll
+        for (int l = 0; l < NLV; ++l)
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            ia[l][h] += __float2int_rn(acc[l][h]);
+            acc[l][h] = 0.f;
+          }
+      }
+    }
+    // G (rho < 8) and W (rho >= 8): the level sums of this tile's outputs
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int rho = (h >> 1) ? rho1 : rho0;
+      const int i = 2 * t + (h & 1);
+      if (rho >= M1) continue;
+      int sl[NLV];
+#pragma unroll
+      for (int l = 0; l < NLV; ++l) sl[l] = ia[l][h] + __float2int_rn(acc[l][h]);
+      const double val = level_value(sl, max(S.colE[j0 + rho], 1) + max(S.colE[j0 + i], 1) - 2084);
+      if (rho < KB) S.G[rho * KB + i] = val;
+      else S.Z[i * MX + j0 + rho] = fma(S.piv[j0 + i], S.Rb[i * MX + j0 + rho], val);
+    }
+  }
+}
+
 }  // namespace blk
 
 // R packed as in the column-owned kernel's output: block blockIdx.x of the stacked R's
@@ -480,7 +596,7 @@ k_tsqr_blk(const double* __restrict__ W, int64_t rows, int64_t ld, const int* __
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   for (int i = tid; i < MX * (MX + 1) / 2; i += NT) S.R[i] = 0.0;
   for (int i = tid; i < NLV * MX * KB; i += NT) S.L1[i] = 0;
-  if (tid < MX) colk::mbar_init(reinterpret_cast<uint64_t*>(&S.bar[tid]), 1);
+  for (int i = tid; i < MX; i += NT) colk::mbar_init(reinterpret_cast<uint64_t*>(&S.bar[i]), 1);
   if (tid == 0) S.abort_flag = 0;
   __syncthreads();
   const int64_t p0 = (int64_t)blockIdx.x * npanels / gridDim.x;
@@ -597,22 +713,200 @@ k_tsqr_blk(const double* __restrict__ W, int64_t rows, int64_t ld, const int* __
   }
 }
 
-size_t tsqr_blk_smem(int m_max) {
-  return m_max <= 64 ? blk::smem_bytes<64, 128>() : blk::smem_bytes<80, 96>();
-}
-int tsqr_blk_rows(int m_max) { return m_max <= 64 ? 128 : 96; }
 
-cudaError_t launch_tsqr_blk(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout,
-                            int64_t ldR, int* status, cudaStream_t s) {
-  if (L.in != Fmt::F64 || L.comp != Fmt::F64 || L.out != Fmt::F64 || L.mmax > 80 ||
-      L.pr != tsqr_blk_rows(L.mmax))
-    return cudaErrorInvalidValue;
-  auto kern = L.mmax <= 64 ? k_tsqr_blk<64, 128, double> : k_tsqr_blk<80, 96, double>;
-  const size_t sm = tsqr_blk_smem(L.mmax);
+// The wide layouts: R in the global slice Rg (packed upper triangle per CTA).
+template <int MX, int PB>
+__global__ void __launch_bounds__(blk::NT, (MX <= 256 ? 2 : 1))
+k_tsqr_blkw(const double* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
+            int m_val, int mmax, double* __restrict__ Rout, int64_t ldR, int mb, int64_t npanels,
+            double* __restrict__ Rscr, int* status) {
+  using namespace blk;
+  constexpr int RPL = PB / 32, NMT = PB / 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemW<MX, PB>& S = *reinterpret_cast<SmemW<MX, PB>*>(smem_raw);
+  const int m = m_ptr ? *m_ptr : m_val;
+  if (m < 1 || m > MX || m > mmax || m > mb || blockDim.x != NT) {
+    if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
+    return;
+  }
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  double* Rg = Rscr + (size_t)blockIdx.x * ((size_t)MX * (MX + 1) / 2);
+  for (int i = tid; i < MX * (MX + 1) / 2; i += NT) Rg[i] = 0.0;
+  for (int i = tid; i < MX; i += NT) colk::mbar_init(reinterpret_cast<uint64_t*>(&S.bar[i]), 1);
+  if (tid == 0) S.abort_flag = 0;
+  __syncthreads();
+  // the block's rows of R between the global slice and shared memory
+  auto stage_in = [&](int j0, int tl, int nthr) {
+    const int kb = min(KB, m - j0);
+    for (int idx = tl; idx < kb * MX; idx += nthr) {
+      const int i = idx / MX, c = idx % MX;
+      if (c >= j0 + i && c < m) S.Rb[i * MX + c] = Rg[rix<MX>(j0 + i, c)];
+    }
+  };
+  auto stage_out = [&](int j0) {
+    const int kb = min(KB, m - j0);
+    for (int idx = tid; idx < kb * MX; idx += NT) {
+      const int i = idx / MX, c = idx % MX;
+      if (c >= j0 + i && c < m) Rg[rix<MX>(j0 + i, c)] = S.Rb[i * MX + c];
+    }
+  };
+  const int64_t p0 = (int64_t)blockIdx.x * npanels / gridDim.x;
+  const int64_t p1 = (int64_t)(blockIdx.x + 1) * npanels / gridDim.x;
+  bool ok = true;
+  for (int64_t p = p0; p < p1 && ok; ++p) {
+    const uint32_t par = (uint32_t)((p - p0) & 1);
+    // the panel, 8 columns per warp at a time (all loads of a group first)
+    for (int c0 = 0; c0 < m; c0 += 8 * NW) {
+      double v[8][RPL];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int c = c0 + w + NW * s;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int64_t row = p * PB + lane + 32 * q;
+          v[s][q] = (c < m && row < rows) ? W[row + (int64_t)c * ld] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int c = c0 + w + NW * s;
+        if (c < m) {
+          int em = 0;
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            S.P[pix<MX>(lane + 32 * q, c)] = v[s][q];
+            em = max(em, efield(v[s][q]));
+          }
+#pragma unroll
+          for (int o = 16; o; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+          if (lane == 0) S.colE[c] = em;
+        }
+      }
+    }
+    if (p + 1 < p1 && (lane & 15) == 0) {
+      for (int c = w; c < m; c += NW) {
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int64_t row = (p + 1) * PB + lane + 32 * q;
+          if (row < rows) asm volatile("prefetch.global.L2 [%0];" ::"l"(W + row + (int64_t)c * ld));
+        }
+      }
+    }
+    stage_in(0, tid, NT);
+    __syncthreads();
+    if (w < 4 && w < min(KB, m)) chain(S, 0, min(KB, m), w, lane, par, status);
+    __syncthreads();
+    for (int j0 = 0;; j0 += KB) {
+      if (*reinterpret_cast<volatile int*>(&S.abort_flag)) {
+        ok = false;
+        break;
+      }
+      if (j0 + KB >= m) {  // the last block: its rows of R go back to the slice
+        stage_out(j0);
+        __syncthreads();
+        break;
+      }
+      prod1w(S, j0, m, w, lane);
+      __syncthreads();
+      for (int c = j0 + KB + tid; c < m; c += NT) {
+        double z[KB];
+        int ez = 0;
+#pragma unroll
+        for (int i = 0; i < KB; ++i) {
+          double acc = S.Z[i * MX + c];
+#pragma unroll
+          for (int q = 0; q < i; ++q) acc = fma(-S.G[q * KB + i], z[q], acc);
+          z[i] = acc * S.rt[j0 + i];
+          S.Z[i * MX + c] = z[i];
+          S.Rb[i * MX + c] = fma(-S.piv[j0 + i], z[i], S.Rb[i * MX + c]);
+          if (z[i] != 0.0) ez = max(ez, ef1(z[i]) + max(S.colE[j0 + i], 1) - 1023);
+        }
+        S.zE[c] = ez;
+        S.colE[c] = 0;
+      }
+      __syncthreads();
+      stage_out(j0);
+      __syncthreads();
+      // the next block's columns of P (warps 0..NMT-1) while warps 4-7 stage its rows of R
+      const int j1 = j0 + KB, kb1 = min(KB, m - j1);
+      if (w < 4) {
+        if (w < NMT) prod2(S, j0, m, w, 0, 1, lane);
+      } else {
+        stage_in(j1, tid - 128, NT - 128);
+      }
+      __syncthreads();
+      // the next block's chain (warps 0-3) beside the rest of P -= X Z (warps 4-7)
+      if (w < 4) {
+        if (w < kb1) chain(S, j1, kb1, w, lane, par, status);
+      } else {
+        constexpr int WPT = 4 / NMT;  // warps per 16-row tile
+        const int u = w - 4;
+        for (int nt = 1 + u / NMT; nt < MX / 8; nt += WPT) prod2(S, j0, m, u % NMT, nt, nt + 1, lane);
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  if (*reinterpret_cast<volatile int*>(&S.abort_flag)) return;
+  for (int idx = tid; idx < mb * m; idx += NT) {
+    const int i = idx % mb, k = idx / mb;
+    const double v = (i < m && i <= k) ? Rg[blk::rix<MX>(i, k)] : 0.0;
+    Rout[(int64_t)blockIdx.x * mb + i + (int64_t)k * ldR] = v;
+  }
+}
+
+// layouts by m_max: (64, 128) and (80, 96) with R in shared memory, (160, 64), (256, 32)
+// and (512, 32) with R in a global slice; two CTAs per SM up to m = 256
+size_t tsqr_blk_smem(int m_max) {
+  if (m_max <= 64) return blk::smem_bytes<64, 128>();
+  if (m_max <= 80) return blk::smem_bytes<80, 96>();
+  if (m_max <= 160) return blk::smem_bytes<160, 64>();
+  if (m_max <= 256) return blk::smem_bytes<256, 32>();
+  return blk::smem_bytes<512, 32>();
+}
+int tsqr_blk_rows(int m_max) {
+  return m_max <= 64 ? 128 : m_max <= 80 ? 96 : m_max <= 160 ? 64 : 32;
+}
+int tsqr_blk_per_sm(int m_max) { return m_max <= 256 ? 2 : 1; }
+size_t tsqr_blk_scratch(int m_max, int64_t ctas) {
+  if (m_max <= 80) return 0;
+  const size_t mx = m_max <= 160 ? 160 : m_max <= 256 ? 256 : 512;
+  return (size_t)ctas * (mx * (mx + 1) / 2) * sizeof(double);
+}
+
+namespace {
+template <class K>
+cudaError_t blk_attrs(K kern, size_t sm) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  // two CTAs per SM: the largest shared-memory carveout
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  // two CTAs per SM where they fit: the largest shared-memory carveout
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+template <int MX, int PB>
+cudaError_t run_blkw(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout, int64_t ldR,
+                     void* Rscr, int* status, cudaStream_t s) {
+  auto kern = k_tsqr_blkw<MX, PB>;
+  const size_t sm = blk::smem_bytes<MX, PB>();
+  cudaError_t e = blk_attrs(kern, sm);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)L.ctas, blk::NT, sm, s>>>(static_cast<const double*>(W), L.rows, ld, m_dev, L.mval, L.mmax,
+                                             static_cast<double*>(Rout), ldR, L.mb, L.panels,
+                                             static_cast<double*>(Rscr), status);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_tsqr_blk(const TsqrLevel& L, const void* W, int64_t ld, const int* m_dev, void* Rout,
+                            int64_t ldR, void* Rscr, int* status, cudaStream_t s) {
+  if (L.in != Fmt::F64 || L.comp != Fmt::F64 || L.out != Fmt::F64 || L.mmax > 512 ||
+      L.pr != tsqr_blk_rows(L.mmax) || (L.mmax > 80 && !Rscr))
+    return cudaErrorInvalidValue;
+  if (L.mmax > 256) return run_blkw<512, 32>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+  if (L.mmax > 160) return run_blkw<256, 32>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+  if (L.mmax > 80) return run_blkw<160, 64>(L, W, ld, m_dev, Rout, ldR, Rscr, status, s);
+  auto kern = L.mmax <= 64 ? k_tsqr_blk<64, 128, double> : k_tsqr_blk<80, 96, double>;
+  const size_t sm = tsqr_blk_smem(L.mmax);
+  cudaError_t e = blk_attrs(kern, sm);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)L.ctas, blk::NT, sm, s>>>(static_cast<const double*>(W), L.rows, ld, m_dev, L.mval,
                                              L.mmax, static_cast<double*>(Rout), ldR, L.mb, L.panels,

@@ -74,14 +74,7 @@ int tsqr_col_pick(int m_max, Fmt in, Fmt comp, Fmt out, int* pr, int* nw, int* p
       const int ov = tune_get(key, -1);
       if (ov >= 0 && ov <= 9 && usable(ov, m_max)) id = ov;
     } else if (f64 && id >= 0) {
-      // native FP64 up to m = 80: the blocked kernel with tensor-core trailing updates
-      if (m_max <= (tune_get("tsqr.blk80", 1) != 0 ? 80 : 64) && tune_get("tsqr.blk64", 1) != 0) {
-        *pr = tsqr_blk_rows(m_max);
-        *nw = 8;
-        *per_sm = 2;
-        return kTsqrBlkId;
-      }
-      // else its own layout per bucket ("tsqr.colcfg64.<bucket>")
+      // native FP64: its own layout per bucket ("tsqr.colcfg64.<bucket>")
       char key[32];
       snprintf(key, sizeof(key), "tsqr.colcfg64.%d", id);
       const int ov = tune_get(key, -1);
@@ -96,7 +89,6 @@ int tsqr_col_pick(int m_max, Fmt in, Fmt comp, Fmt out, int* pr, int* nw, int* p
 }
 
 size_t tsqr_col_smem(int m_max, Fmt comp, int id) {
-  if (id == kTsqrBlkId) return tsqr_blk_smem(m_max);
   // mbarriers and abort flag (64 bytes), packed R, two pivot slots
   const size_t tri = (size_t)m_max * (m_max + 1) / 2;
   return 64 + (tri + 2 * (size_t)(32 * kCol[id].prl + 2)) * fmt_bytes(comp);

@@ -12,7 +12,6 @@ cudaError_t tsqr_col_upper(const TsqrLevel& L, const void* W, int64_t ld, const 
     // the autotuner's alternative layouts (ids 5-9) for native FP64 as well
     using colk::run_col;
     using D = double;
-    if (L.cfg == kTsqrBlkId) return launch_tsqr_blk(L, W, ld, m_dev, Rout, ldR, status, s);
     switch (L.cfg) {
       case 5: return run_col<12, 6, 8, 1, D, D, D>(L, W, ld, m_dev, Rout, ldR, status, s);
       case 6: return run_col<16, 4, 4, 1, D, D, D>(L, W, ld, m_dev, Rout, ldR, status, s);

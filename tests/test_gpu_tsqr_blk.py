@@ -35,7 +35,11 @@ def sign_fixed(R):
 CASES = [(128, 17), (129, 20), (1000, 24), (4096, 33), (20000, 48), (12345, 63), (100000, 64),
          (9, 40), (64, 64), (1 << 20, 64),
          # the 96-row layout for 64 < m <= 80 (the m = 80 steps of an 8^d tensor at r_max = 10)
-         (96, 80), (97, 65), (5000, 72), (100000, 80), (30, 80), (1 << 19, 80)]
+         (96, 80), (97, 65), (5000, 72), (100000, 80), (30, 80), (1 << 19, 80),
+         # the wide layouts (R in a global slice per CTA): 64-row panels up to m = 160,
+         # 32-row panels up to 256 and 512 (one CTA per SM)
+         (64, 96), (20000, 120), (100000, 160), (65, 161), (3000, 200), (20000, 256),
+         (4000, 300), (20000, 400), (2000, 512), (9, 300)]
 
 
 @pytest.mark.parametrize("rows,m", CASES)
@@ -50,16 +54,16 @@ def test_blocked_tsqr_matches_oracle(rows, m):
     s_got = np.linalg.svd(R, compute_uv=False)[: len(s_ref)]
     assert np.max(np.abs(s_got - s_ref)) <= 1e-13 * s_ref[0]
     if rows >= m and rows <= 100000:
-        Ro = tsqr_flat(W, 64)
+        Ro = tsqr_flat(W, max(64, m))
         assert np.max(np.abs(sign_fixed(R) - sign_fixed(Ro))) <= 1e-12 * nw
 
 
-@pytest.mark.parametrize("m", [64, 80])
-def test_blocked_equals_column_kernel(m):
+@pytest.mark.parametrize("m,rows", [(64, 300000), (80, 300000), (160, 100000), (256, 30000), (400, 20000)])
+def test_blocked_equals_column_kernel(m, rows):
     # the same FP64 Householder sequence with the block transformations on the tensor cores:
-    # R agrees with the column-owned kernel's R to FP64 rounding
+    # R agrees with the FP64 panel kernels' R (blocked kernel off) to FP64 rounding
     rng = np.random.default_rng(5)
-    W = rng.standard_normal((300000, m)) + 3.0
+    W = rng.standard_normal((rows, m)) + 3.0
     Rb = api.tsqr(colmajor(W), arith="f64").cpu().numpy()
     capi.tt_tune_set("tsqr.blk64", 0)
     try:
@@ -69,7 +73,7 @@ def test_blocked_equals_column_kernel(m):
     assert np.max(np.abs(sign_fixed(Rb) - sign_fixed(Rc))) <= 1e-13 * np.linalg.norm(W)
 
 
-@pytest.mark.parametrize("span,m", [(0, 64), (60, 64), (300, 64), (300, 80)])
+@pytest.mark.parametrize("span,m", [(0, 64), (60, 64), (300, 64), (300, 80), (300, 160), (300, 256)])
 def test_blocked_tsqr_column_scaling(span, m):
     # W = G 2^s_c: R(W) = R(G) 2^s_c up to row signs, whatever the exponents
     rng = np.random.default_rng(span + 11)
@@ -78,7 +82,7 @@ def test_blocked_tsqr_column_scaling(span, m):
     W = np.ldexp(G, s[None, :])
     R = api.tsqr(colmajor(W), arith="f64").cpu().numpy()
     Rg = np.ldexp(R, -s[None, :])
-    Ro = tsqr_flat(G, m)
+    Ro = tsqr_flat(G, max(64, m))
     assert np.max(np.abs(sign_fixed(Rg) - sign_fixed(Ro))) <= 1e-12 * np.linalg.norm(G)
 
 
@@ -108,9 +112,10 @@ def run_f64(X, r_max):
     return plan.result()
 
 
-@pytest.mark.parametrize("dims,r_max", [((8,) * 7, 8), ((4,) * 9, 6), ((6, 7, 8, 9, 5), 20), ((8,) * 6, 10)])
+@pytest.mark.parametrize("dims,r_max", [((8,) * 7, 8), ((4,) * 9, 6), ((6, 7, 8, 9, 5), 20), ((8,) * 6, 10),
+                                        ((8,) * 6, 20), ((8,) * 6, 32), ((8,) * 6, 50)])
 def test_tt_svd_native_fp64_with_blocked_tsqr(dims, r_max):
-    # the whole native FP64 path with the blocked first levels (unfoldings of 24..80
+    # the whole native FP64 path with the blocked first levels (unfoldings of 24..400
     # columns), against the Alg. 1 oracle at the FP64 form's bar
     X = uniform_tensor(dims, seed=sum(dims) * r_max)
     res = run_f64(X, r_max)
