@@ -69,7 +69,7 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=4.0)
     p.add_argument("--serve-only", action="store_true", help="only the serving leg (both admission orders)")
     p.add_argument("--case", default="", help="one building block for profiling instead of the bench: "
-                   "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix), tsqr64:ROWS:M (native FP64), ttsvd32:N:D:RMAX (FP32 form), "
+                   "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix), tsqr64:ROWS:M (native FP64), ttsvd32:N:D:RMAX (FP32 form), fma (ALU rate probes), "
                    "tsmm:ROWS:M:K (W V(:, 0:K) of a uniform FP64 W) or svd:M (small SVD of a "
                    "uniform upper-triangular R) or ttsvd:N:D:RMAX:ARITH (a whole TT-SVD of a "
                    "uniform N^D FP64 tensor, ARITH f64 or df), each optionally followed by "
@@ -296,6 +296,14 @@ def run_case(spec: str) -> int:
         X = api.gen_uniform(n ** d, 3, torch.float32)
         plan = api.TTSVDPlan([n] * d, r, 0.0, torch.float32, "df")
         call = lambda: plan.run(X)
+    elif parts[0] == "fma":
+        # fma -- the library's multiply-add rate probes (the ALU peaks of the rooflines)
+        rates = {"fp32_tflops": capi.tt_fma_rate(capi.FMA_FP32) / 1e12,
+                 "fp64_tflops": capi.tt_fma_rate(capi.FMA_FP64) / 1e12,
+                 "float_float_tflops_fp64eq": capi.tt_fma_rate(capi.FMA_DF) / 1e12,
+                 "fp64_mma_tflops": capi.tt_fma_rate(capi.FMA_MMA_FP64) / 1e12}
+        print(json.dumps({"case": spec, **rates}), flush=True)
+        return 0
     elif parts[0] == "svd":
         m = int(parts[1])
         g = torch.Generator(device="cuda").manual_seed(0)
