@@ -301,7 +301,7 @@ def run_case(spec: str) -> int:
         rates = {"fp32_tflops": capi.tt_fma_rate(capi.FMA_FP32) / 1e12,
                  "fp64_tflops": capi.tt_fma_rate(capi.FMA_FP64) / 1e12,
                  "float_float_tflops_fp64eq": capi.tt_fma_rate(capi.FMA_DF) / 1e12,
-                 "fp64_mma_tflops": capi.tt_fma_rate(capi.FMA_MMA_FP64) / 1e12}
+                 "fp64_mma_tflops": capi.tt_fma_rate(capi.MMA_FP64) / 1e12}
         print(json.dumps({"case": spec, **rates}), flush=True)
         return 0
     elif parts[0] == "svd":
