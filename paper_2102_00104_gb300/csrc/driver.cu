@@ -171,7 +171,11 @@ static TsqrLevel make_level(int64_t rows, int m_max, Fmt in, Fmt comp, Fmt out, 
       // tree (m^3 / 6 per pair, log2 P deep) more and shorter first-level panels pay.
       const bool merges = m_max >= tune_get("tsqr.merge_m", 96);
       // rows per CTA >= q4 m / 4 (measured best: m rows for m >= 200, 2 m below)
-      const int64_t q4 = merges ? std::max(1, tune_get("tsqr.pcap_q", m_max >= 200 ? 4 : 8)) : 16;
+      // (FP32 panels at m >= 200: 8x fewer first-level R's than float-float and FP64 -- the
+      // FP32 panels are cheap, the float-float tree above them is not: measured on the
+      // 8^10 FP32 form at r_max = 32, 128.6 ms against 138.0 ms with the float-float setting)
+      const int q_def = m_max >= 200 ? (comp == Fmt::F32 ? tune_get("tsqr.pcap_q32", 32) : 4) : 8;
+      const int64_t q4 = merges ? std::max(1, tune_get("tsqr.pcap_q", q_def)) : 16;
       const int64_t p_cap = std::max<int64_t>(1, 4 * rows / (q4 * (int64_t)m_max));
       ctas = std::min<int64_t>(std::min<int64_t>(L.panels, (int64_t)nsm * cta_per_sm), p_cap);
       if (ctas_override > 0) ctas = std::min<int64_t>(L.panels, ctas_override);
