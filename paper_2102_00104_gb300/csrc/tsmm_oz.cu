@@ -39,7 +39,7 @@ constexpr int OZ_WARPS = 4;
 constexpr int OZ_THREADS = 32 * OZ_WARPS;
 constexpr int OZ_CS = OZ_TR * 8 + 32;   // bytes per staged column (padded: conflict-free reads)
 constexpr int OZ_MAXM = 96;             // sum of one level over k stays below 2^24
-constexpr int OZ_MAXR = 32;
+constexpr int OZ_MAXR = 64;   // r_max > 32 runs as two launches of up to 32 columns (oz_col0)
 
 __device__ __forceinline__ void oz_mma(float (&c)[4], const uint32_t (&a)[4], uint2 b) {
   asm volatile(
@@ -62,13 +62,19 @@ __global__ void __launch_bounds__(OZ_THREADS)
 k_tsmm_oz(const S* __restrict__ W, int64_t rows, int64_t ld, const int* __restrict__ m_ptr,
           int m_val, const VS* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
           SO* __restrict__ Y, int64_t ldy, int m_max, int r_max, int nbuf, int* status,
-          const XRange* xr) {
+          const XRange* xr, int col0) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   XRead<df, S> rd;  // W read as W 2^-sh (FP64 input of the float-float form)
   rd.set(xr ? xr->k : 0, xr != nullptr);
   const int m = m_ptr ? *m_ptr : m_val;
-  const int r = r_ptr ? *r_ptr : r_val;
-  if (m < 1 || m > m_max || m_max > OZ_MAXM || r < 1 || r > r_max || r > m || r > 8 * NT ||
+  const int r_all = r_ptr ? *r_ptr : r_val;
+  // this launch's columns: col0 .. col0 + 8 NT - 1 of V and Y (the second launch of an
+  // r_max > 32 product has nothing to do when the rank found is <= 32)
+  if (col0 > 0 && r_all <= col0) return;
+  const int r = min(r_all - col0, 8 * NT);
+  V += (size_t)col0 * ldV;
+  Y += (int64_t)col0 * ldy;
+  if (m < 1 || m > m_max || m_max > OZ_MAXM || r < 1 || r_all > r_max || r_all > m || r > 8 * NT ||
       nbuf < 1 || nbuf > 2) {
     if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
     return;
@@ -335,7 +341,7 @@ bool tsmm_oz_ok(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max) {
 }
 
 size_t tsmm_oz_smem(int m_max, int r_max, int nbuf, bool x64) {
-  const int nt = r_max <= 8 ? 1 : (r_max <= 16 ? 2 : 4);
+  const int nt = r_max <= 8 ? 1 : (r_max <= 16 ? 2 : 4);  // per launch (r_max > 32: 4)
   const int kt = (m_max + 15) / 16;
   const int nd = x64 ? 7 : 6;
   return nbuf * (size_t)m_max * OZ_CS + (size_t)kt * nd * nt * 32 * sizeof(uint2) + 8 * nt * sizeof(int) + 16;
@@ -349,11 +355,16 @@ cudaError_t run_oz(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld, co
   auto k = k_tsmm_oz<NT, X64, S, VS, SO>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)c.ctas, OZ_THREADS, c.smem, s>>>(static_cast<const S*>(W), rows, ld, m_dev, c.m_max,
-                                                 static_cast<const VS*>(V), ldV, r_dev, c.r_max,
-                                                 static_cast<SO*>(Y), ldy, c.m_max, c.r_max, c.rc,
-                                                 status, c.xr);
-  return cudaGetLastError();
+  // up to 32 columns per launch: r_max > 32 takes a second launch for columns 32..r-1
+  for (int col0 = 0; col0 < c.r_max; col0 += 8 * NT) {
+    k<<<(unsigned)c.ctas, OZ_THREADS, c.smem, s>>>(static_cast<const S*>(W), rows, ld, m_dev, c.m_max,
+                                                   static_cast<const VS*>(V), ldV, r_dev, c.r_max,
+                                                   static_cast<SO*>(Y), ldy, c.m_max, c.r_max, c.rc,
+                                                   status, c.xr, col0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <class S, class VS, class SO, bool X64 = false>

@@ -346,7 +346,7 @@ cudaError_t run_tc_nn(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
 
 // usable for these formats and sizes ("tsmm.tc" 0 never, 1 where tsmm_oz would run)
 bool tsmm_tc_ok(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max) {
-  if (tune_get("tsmm.tc", 0) == 0) return false;
+  if (tune_get("tsmm.tc", 0) == 0 || r_max > 32) return false;
   if (!tsmm_oz_ok(in, comp, vfmt, out, m_max, r_max)) return false;
   if (m_max > TC_MAXM || r_max > 16) return false;
   // dynamic shared memory plus the 2 KB of the static row-key array

@@ -26,7 +26,9 @@ def exact_rows(W, V, rows, k):
 
 @pytest.mark.parametrize("rows,m,k,scale", [(100000, 64, 10, 1.0), (70001, 80, 32, 1e-30),
                                             (5000, 96, 7, 3e20), (4096, 17, 1, 1.0), (3000, 12, 5, 1.0),
-                                            (20000, 64, 10, 1e-280), (20000, 64, 10, 1e280)])
+                                            (20000, 64, 10, 1e-280), (20000, 64, 10, 1e280),
+                                            # r > 32: two launches of up to 32 columns
+                                            (30000, 64, 50, 1.0), (4096, 96, 64, 1.0), (3000, 40, 33, 1.0)])
 def test_native_fp64_product_is_fp64_accurate(rows, m, k, scale):
     ensure_lib()
     rng = np.random.default_rng(rows + m)
