@@ -119,3 +119,33 @@ def test_full_size_8p10_planted_rank16(r_max, arith):
     assert abs(err2 - res.err2) <= 1e-12 * nx2, (err2, res.err2, nx2)
     # rank >= 16 keeps the planted part: only noise is discarded, 9 steps at most 1e-12 each
     assert err2 <= 9e-12 * nx2, err2 / nx2
+
+
+def test_full_size_8p10_rmax10_native_fp64():
+    # the headline arithmetic at full size: the same 8^10 tensor in native FP64 (blocked
+    # tensor-core TSQR, FP64-accurate W V_r), held to FP64 bars: sigma of step 9 against the
+    # singular values of the R of a library Householder QR of the 2^24 x 64 unfolding (a Gram
+    # spectrum would lose ~1e-12 of sigma_max on the smallest values) to 1e-12 sigma_max,
+    # cores orthonormal to 1e-14 m, ||X - X~||^2 equal to the reported discarded energy to
+    # 1e-12 ||X||^2 (X~ contracted on the device)
+    ensure_lib()
+    dims, r_max = (8,) * 10, 10
+    X = api.gen_uniform(8 ** 10, 0, torch.float64)
+    plan = api.TTSVDPlan(dims, r_max, 0.0, torch.float64, "f64", want_sigma=True)
+    plan.run(X)
+    res = plan.result()
+    assert res.ranks == O.planned_ranks(list(dims), r_max)
+    M = X.view(64, 8 ** 8)
+    R = torch.linalg.qr(M.t(), mode="r").R
+    del M
+    s_ref = torch.linalg.svdvals(R).cpu().numpy()
+    got = res.sigma[9].cpu().numpy()[:64]
+    assert np.max(np.abs(got - s_ref)) <= 1e-12 * s_ref[0], np.max(np.abs(got - s_ref)) / s_ref[0]
+    nx2 = float(torch.dot(X, X).item())
+    for c in res.core_arrays()[1:]:
+        assert O.core_orthonormality_defect(c) <= 1e-14 * 80
+    Xt = tt_full_dev([c.to(torch.float64) for c in res.cores], dims)
+    d = X - Xt
+    del Xt
+    err2 = float(torch.dot(d, d).item())
+    assert abs(err2 - res.err2) <= 1e-12 * nx2, (err2, res.err2, nx2)
