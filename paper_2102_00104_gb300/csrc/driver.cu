@@ -367,6 +367,7 @@ static tt_status build_plan(int d, const int64_t* n, int r_max, double tol, tt_d
   P.szR = 0;
   P.szRscr = 0;
   P.m_all_max = 1;
+  size_t wide_g = 0;  // the wide Jacobi's working copy where it leaves shared memory
   for (int i = d; i >= 2; --i) {
     StepPlan S;
     S.i = i;
@@ -383,6 +384,7 @@ static tt_status build_plan(int d, const int64_t* n, int r_max, double tol, tt_d
       const bool first_active = P.szR == 0;  // no TSQR planned yet
       S.wide = !first_active && rows < S.m_max && tune_get("svd.wide", 1) &&
                jacobi_wide_fits(P.comp_svd, (int)rows, S.m_max);
+      if (S.wide) wide_g = std::max(wide_g, jacobi_wide_gbytes(P.comp_svd, (int)rows, S.m_max));
       if (!S.wide) {
         S.levels = plan_tsqr(rows, S.m_max, cur, P.comp_tsqr1, P.comp_tsqr2, nsm, ctas_override,
                              first_active ? P.in_chunks : 1);
@@ -403,7 +405,7 @@ static tt_status build_plan(int d, const int64_t* n, int r_max, double tol, tt_d
   }
   const int mp = P.m_all_max + (P.m_all_max & 1);
   P.ldA = mp;
-  P.szJ = jacobi_scratch_bytes(P.comp_svd, P.m_all_max);
+  P.szJ = std::max(jacobi_scratch_bytes(P.comp_svd, P.m_all_max), wide_g);
   P.szVout = (size_t)mp * mp * fmt_bytes(P.comp_svd);
   size_t off = 0;
   P.off_state = off; off += align256(sizeof(DevState));
@@ -739,7 +741,7 @@ static tt_status run_plan(const Plan& P, const void* X, double* const* cores_out
     if (S.wide) {
       prof::Scope ps(2, i, (double)rows * mm * fmt_bytes(cur_fmt), 0.0, s, &st->sweeps[i]);
       TT_CK(launch_jacobi_wide(P.comp_svd, cur_fmt, cur, rows, (int)rows, &st->m[i], S.m_max, sig,
-                               Vout, P.ldA, status, &st->sweeps[i], s));
+                               Vout, P.ldA, status, &st->sweeps[i], wb + P.off_A, s));
       ++g_launches;
     } else {
       // TSQR levels

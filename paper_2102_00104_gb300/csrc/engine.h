@@ -154,7 +154,9 @@ size_t jacobi_scratch_bytes(Fmt comp, int m_max);
 bool jacobi_wide_fits(Fmt comp, int rows, int m_max);
 cudaError_t launch_jacobi_wide(Fmt comp, Fmt win, const void* W, int64_t ldW, int rows,
                                const int* m_dev, int m_max, double* sigma, void* Vout, int ldV,
-                               int* status, int* sweeps_out, cudaStream_t s);
+                               int* status, int* sweeps_out, void* gscr, cudaStream_t s);
+// global scratch for the wide Jacobi's working copy when it does not fit shared memory (else 0)
+size_t jacobi_wide_gbytes(Fmt comp, int rows, int m_max);
 // cluster form (svd_cluster.cu): cluster size for m (0 = single CTA) and its launch
 int jacobi_cluster_plan(Fmt comp, int m_max, int* npl_out);
 // block-cyclic cluster kernel: cluster size (0 if it does not apply) and columns per block

@@ -265,7 +265,7 @@ template <class C, class WI, int G>
 __global__ void __launch_bounds__(1024)
 k_jacobi_wide(const WI* __restrict__ W, int64_t ldW, int rows, const int* __restrict__ m_ptr,
               int m_max, int lda, double* __restrict__ sigma, C* __restrict__ Vout, int ldV,
-              int* status, int* sweeps_out, int max_sweeps) {
+              int* status, int* sweeps_out, int max_sweeps, C* __restrict__ Aglob) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_rot;
   __shared__ int s_cos;
@@ -277,8 +277,10 @@ k_jacobi_wide(const WI* __restrict__ W, int64_t ldW, int rows, const int* __rest
     if (threadIdx.x == 0 && status) atomicOr(status, DEV_ERR_SHAPE);
     return;
   }
-  C* A = reinterpret_cast<C*>(smem_raw);          // column p (= row p of W) at A + p * lda
-  C* nrm = A + (size_t)ncp * lda;                 // ||a_k||^2
+  // column p (= row p of W) at A + p * lda: in shared memory, or (when rows x m does not
+  // fit there) in an L2-resident global scratch that only this CTA touches
+  C* A = Aglob ? Aglob : reinterpret_cast<C*>(smem_raw);
+  C* nrm = Aglob ? reinterpret_cast<C*>(smem_raw) : A + (size_t)ncp * lda;  // ||a_k||^2
   int* defi = reinterpret_cast<int*>(nrm + ncp);  // by rank: 1 = completion needed
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nwarps = nt >> 5;
@@ -751,21 +753,24 @@ cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const i
 }
 
 bool jacobi_wide_fits(Fmt comp, int rows, int m_max) {
-  if (rows < 1 || rows >= m_max || m_max > kMaxM || (comp != Fmt::DF && comp != Fmt::F64))
-    return false;
+  return rows >= 1 && rows < m_max && m_max <= kMaxM && (comp == Fmt::DF || comp == Fmt::F64);
+}
+// global scratch the wide kernel needs for its working copy (0: it fits in shared memory)
+size_t jacobi_wide_gbytes(Fmt comp, int rows, int m_max) {
   const size_t es = fmt_bytes(comp);
   const int ncp = rows + (rows & 1);
   const size_t need = (size_t)ncp * m_max * es + (size_t)ncp * (es + sizeof(int));
-  return need <= max_smem_optin() - 4096;
+  return need <= max_smem_optin() - 4096 ? 0 : (size_t)ncp * m_max * es;
 }
 
 template <class C, class WI, int G>
 static cudaError_t run_wide_g(const void* W, int64_t ldW, int rows, const int* m_dev, int m_max,
                               double* sigma, void* Vout, int ldV, int* status, int* sweeps_out,
-                              cudaStream_t s) {
+                              void* gscr, cudaStream_t s) {
   const int ncp = rows + (rows & 1);
   const size_t es = sizeof(C);
-  const size_t smem = (size_t)ncp * m_max * es + (size_t)ncp * (es + sizeof(int));
+  const bool glob = gscr != nullptr;
+  const size_t smem = (glob ? 0 : (size_t)ncp * m_max * es) + (size_t)ncp * (es + sizeof(int));
   int threads = ((ncp / 2) * G + 31) / 32 * 32;
   if (threads < 64) threads = 64;
   if (threads > 1024) threads = 1024;
@@ -776,33 +781,37 @@ static cudaError_t run_wide_g(const void* W, int64_t ldW, int rows, const int* m
     if (e != cudaSuccess) return e;
   }
   k<<<1, threads, smem, s>>>(static_cast<const WI*>(W), ldW, rows, m_dev, m_max, m_max, sigma,
-                             static_cast<C*>(Vout), ldV, status, sweeps_out, 60);
+                             static_cast<C*>(Vout), ldV, status, sweeps_out, 60,
+                             static_cast<C*>(gscr));
   return cudaGetLastError();
 }
 
 template <class C, class WI>
 static cudaError_t run_wide(const void* W, int64_t ldW, int rows, const int* m_dev, int m_max,
                             double* sigma, void* Vout, int ldV, int* status, int* sweeps_out,
-                            cudaStream_t s) {
+                            void* gscr, cudaStream_t s) {
   // lanes per column pair: about 8-16 elements of a column per lane
   const int g = tune_get("svd.wide_g", m_max >= 256 ? 32 : m_max >= 64 ? 16 : 8);
-  if (g == 32) return run_wide_g<C, WI, 32>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
-  if (g == 16) return run_wide_g<C, WI, 16>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
-  return run_wide_g<C, WI, 8>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+  if (g == 32) return run_wide_g<C, WI, 32>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, gscr, s);
+  if (g == 16) return run_wide_g<C, WI, 16>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, gscr, s);
+  return run_wide_g<C, WI, 8>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, gscr, s);
 }
 
 cudaError_t launch_jacobi_wide(Fmt comp, Fmt win, const void* W, int64_t ldW, int rows,
                                const int* m_dev, int m_max, double* sigma, void* Vout, int ldV,
-                               int* status, int* sweeps_out, cudaStream_t s) {
+                               int* status, int* sweeps_out, void* gscr, cudaStream_t s) {
   if (!jacobi_wide_fits(comp, rows, m_max)) return cudaErrorInvalidValue;
+  // the working copy in shared memory when it fits, else in gscr (jacobi_wide_gbytes)
+  void* g = jacobi_wide_gbytes(comp, rows, m_max) ? gscr : nullptr;
+  if (jacobi_wide_gbytes(comp, rows, m_max) && !gscr) return cudaErrorInvalidValue;
   if (comp == Fmt::DF && win == Fmt::DF)
-    return run_wide<df, df>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+    return run_wide<df, df>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, g, s);
   if (comp == Fmt::DF && win == Fmt::F64)
-    return run_wide<df, double>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+    return run_wide<df, double>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, g, s);
   if (comp == Fmt::DF && win == Fmt::F32)
-    return run_wide<df, float>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+    return run_wide<df, float>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, g, s);
   if (comp == Fmt::F64 && win == Fmt::F64)
-    return run_wide<double, double>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, s);
+    return run_wide<double, double>(W, ldW, rows, m_dev, m_max, sigma, Vout, ldV, status, sweeps_out, g, s);
   return cudaErrorInvalidValue;
 }
 

@@ -135,6 +135,21 @@ def test_fp32_form_parity(dims, r_max):
     compare(X32, res, O.tt_svd(X32, r_max), 1e-5)
 
 
+# wide unfoldings whose one-sided Jacobi working copy (rows x m values) exceeds shared memory:
+# (8, 8, 8, 4, 8, 8) at r_max = 64 has a 64 x 512 step (256 KB in float-float or FP64), whose
+# copy then lives in the workspace
+@pytest.mark.parametrize("dtype,arith", [(torch.float64, "df"), (torch.float64, "f64"), (torch.float32, "df")])
+def test_wide_step_beyond_shared_memory(dtype, arith):
+    dims = (8, 8, 8, 4, 8, 8)
+    X = planted_tt(dims, 20, seed=7, noise_rel=1e-3)
+    if dtype == torch.float32:
+        X = X.astype(np.float32).astype(np.float64)
+    res = run_gpu(X, 64, dtype=dtype, arith=arith)
+    ref = O.tt_svd(X, 64)
+    assert max(ref.ranks) == 64
+    compare(X, res, ref, 1e-10 if dtype == torch.float64 else 1e-5)
+
+
 def test_repeated_runs_are_identical():
     X = uniform_tensor((4,) * 10, seed=2)
     plan = api.TTSVDPlan(X.shape, 8, 0.0, torch.float64, "df", want_sigma=True)
