@@ -165,9 +165,12 @@ cudaError_t launch_jacobi_block(Fmt comp, Fmt rin, const void* R, int64_t ldR, c
                                 int m_max, int nc, int npl, double* sigma, void* Vout, int ldV,
                                 int* status, int* sweeps_out, cudaStream_t s);
 int jacobi_cluster_npl(Fmt comp, int m_max, int nc);
+// Vg / ldVg: global scratch (ldVg >= m_max, m_max columns) for V when A and V do not both fit
+// in the cluster's shared memory
 cudaError_t launch_jacobi_cluster(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
                                   int m_max, int nc, int npl, double* sigma, void* Vout, int ldV,
-                                  int* status, int* sweeps_out, cudaStream_t s);
+                                  int* status, int* sweeps_out, void* Vg, int ldVg, cudaStream_t s);
+bool jacobi_cluster_vg(Fmt comp, int m_max, int npl);
 
 // ---- rank choice / cores --------------------------------------------------------
 cudaError_t launch_truncate(const double* sigma, int64_t rows, int step_i, int n_next,

@@ -729,7 +729,7 @@ cudaError_t launch_jacobi(Fmt comp, Fmt rin, const void* R, int64_t ldR, const i
       const int np = cand == nc ? npl : jacobi_cluster_npl(comp, m_max, cand);
       if (!np) continue;
       const cudaError_t e = launch_jacobi_cluster(comp, rin, R, ldR, m_dev, m_max, cand, np, sigma,
-                                                  Vout, ldV, status, sweeps_out, s);
+                                                  Vout, ldV, status, sweeps_out, Vg, ldA, s);
       if (e == cudaSuccess) return e;
       cudaGetLastError();  // launch refused (no resident cluster of that size)
     }

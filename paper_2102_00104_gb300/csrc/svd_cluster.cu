@@ -71,12 +71,15 @@ template <> __device__ __forceinline__ float ctol<df>(int m) { return 2.0e-14f *
 template <> __device__ __forceinline__ float ctol<double>(int m) { return 2.5e-16f * (float)(m < 8 ? 8 : m); }
 
 // shared memory per CTA: NSLOT column slots of A (m entries) and V (m entries), with
-// NSLOT = 2 npl + 4 (working slots, receive buffers top/bottom x round parity)
-template <class C, class RI, int G>
+// NSLOT = 2 npl + 4 (working slots, receive buffers top/bottom x round parity).  VG: V stays
+// in global memory (Vg, column = the logical column id), for m where A and V together do not
+// fit: a column of V is only ever touched by the CTA holding the matching column of A, and
+// moves between CTAs are ordered by the cluster barriers, so only A's columns travel.
+template <class C, class RI, int G, bool VG>
 __global__ void __launch_bounds__(512)
 k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_ptr, int m_max,
                  int npl, double* __restrict__ sigma, C* __restrict__ Vout, int ldV, int* status,
-                 int* sweeps_out, int max_sweeps) {
+                 int* sweeps_out, int max_sweeps, C* __restrict__ Vg, int ldVg) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int tslot[64], bslot[64];
@@ -95,8 +98,8 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
     return;  // uniform over the cluster: every CTA sees the same m, npl and NC
   }
   C* Acol = reinterpret_cast<C*>(smem_raw);              // slot k: Acol[k * m_max + i]
-  C* Vcol = Acol + (size_t)nslot * m_max;                // slot k: Vcol[k * m_max + i]
-  int* colid = reinterpret_cast<int*>(Vcol + (size_t)nslot * m_max);  // colid[slot]: column id
+  C* Vcol = Acol + (size_t)nslot * m_max;                // slot k: Vcol[k * m_max + i] (!VG)
+  int* colid = reinterpret_cast<int*>(VG ? Vcol : Vcol + (size_t)nslot * m_max);  // column id
   double* allnorm = reinterpret_cast<double*>(colid + ((nslot + 1) & ~1));  // allnorm[MP]
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nwarps = nt >> 5;
@@ -129,7 +132,11 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
       C a = Tr<C>::zero();
       if (col < m && i <= col) a = flush_tiny(pow2s<C>(ld_as<C>(R[i + (int64_t)col * ldR]), -ex));
       Acol[(size_t)k * m_max + i] = a;
-      Vcol[(size_t)k * m_max + i] = (i == col) ? Tr<C>::one() : Tr<C>::zero();
+      if constexpr (VG) {
+        if (col < m) Vg[i + (size_t)col * ldVg] = (i == col) ? Tr<C>::one() : Tr<C>::zero();
+      } else {
+        Vcol[(size_t)k * m_max + i] = (i == col) ? Tr<C>::one() : Tr<C>::zero();
+      }
     }
   }
   float fro = 0.f;
@@ -154,10 +161,10 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
 
   // neighbour receive buffers through distributed shared memory
   C* nextA = c + 1 < NC ? cl.map_shared_rank(Acol, c + 1) : nullptr;
-  C* nextV = c + 1 < NC ? cl.map_shared_rank(Vcol, c + 1) : nullptr;
+  C* nextV = !VG && c + 1 < NC ? cl.map_shared_rank(Vcol, c + 1) : nullptr;
   int* nextId = c + 1 < NC ? cl.map_shared_rank(colid, c + 1) : nullptr;
   C* prevA = c > 0 ? cl.map_shared_rank(Acol, c - 1) : nullptr;
-  C* prevV = c > 0 ? cl.map_shared_rank(Vcol, c - 1) : nullptr;
+  C* prevV = !VG && c > 0 ? cl.map_shared_rank(Vcol, c - 1) : nullptr;
   int* prevId = c > 0 ? cl.map_shared_rank(colid, c - 1) : nullptr;
   int* flags0 = cl.map_shared_rank(&s_flags[0][0], 0);
 
@@ -190,8 +197,8 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
           if (zf < 0.f) tf = -tf;
           C cs, sn;
           rotcs(tf, cs, sn);
-          C* vp = Vcol + (size_t)tslot[i] * m_max;
-          C* vq = Vcol + (size_t)bslot[i] * m_max;
+          C* vp = VG ? Vg + (size_t)colid[tslot[i]] * ldVg : Vcol + (size_t)tslot[i] * m_max;
+          C* vq = VG ? Vg + (size_t)colid[bslot[i]] * ldVg : Vcol + (size_t)bslot[i] * m_max;
           for (int r = gl; r < m; r += G) {
             const C x = ap[r], y = aq[r];
             ap[r] = fnmac(sn, y, mul(cs, x));
@@ -209,7 +216,7 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
         const int src = tslot[npl - 1], dst = RT0 + par;
         for (int r = tid; r < m; r += nt) {
           nextA[(size_t)dst * m_max + r] = Acol[(size_t)src * m_max + r];
-          nextV[(size_t)dst * m_max + r] = Vcol[(size_t)src * m_max + r];
+          if constexpr (!VG) nextV[(size_t)dst * m_max + r] = Vcol[(size_t)src * m_max + r];
         }
         if (tid == 0) nextId[dst] = colid[src];
       }
@@ -217,7 +224,7 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
         const int src = bslot[0], dst = RB0 + par;
         for (int r = tid; r < m; r += nt) {
           prevA[(size_t)dst * m_max + r] = Acol[(size_t)src * m_max + r];
-          prevV[(size_t)dst * m_max + r] = Vcol[(size_t)src * m_max + r];
+          if constexpr (!VG) prevV[(size_t)dst * m_max + r] = Vcol[(size_t)src * m_max + r];
         }
         if (tid == 0) prevId[dst] = colid[src];
       }
@@ -229,9 +236,11 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
         // freed: oldT (sent right), oldB (sent left); received: top from c-1, bottom from c+1
         for (int r = tid; r < m; r += nt) {
           Acol[(size_t)oldT * m_max + r] = Acol[(size_t)(RT0 + par) * m_max + r];
-          Vcol[(size_t)oldT * m_max + r] = Vcol[(size_t)(RT0 + par) * m_max + r];
           Acol[(size_t)oldB * m_max + r] = Acol[(size_t)(RB0 + par) * m_max + r];
-          Vcol[(size_t)oldB * m_max + r] = Vcol[(size_t)(RB0 + par) * m_max + r];
+          if constexpr (!VG) {
+            Vcol[(size_t)oldT * m_max + r] = Vcol[(size_t)(RT0 + par) * m_max + r];
+            Vcol[(size_t)oldB * m_max + r] = Vcol[(size_t)(RB0 + par) * m_max + r];
+          }
         }
         if (tid == 0) {
           colid[oldT] = colid[RT0 + par];
@@ -241,14 +250,14 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
         // freed: oldT (sent right); bottom(0) moves to top(1); received: bottom from CTA 1
         for (int r = tid; r < m; r += nt) {
           Acol[(size_t)oldT * m_max + r] = Acol[(size_t)(RB0 + par) * m_max + r];
-          Vcol[(size_t)oldT * m_max + r] = Vcol[(size_t)(RB0 + par) * m_max + r];
+          if constexpr (!VG) Vcol[(size_t)oldT * m_max + r] = Vcol[(size_t)(RB0 + par) * m_max + r];
         }
         if (tid == 0) colid[oldT] = colid[RB0 + par];
       } else if (c + 1 == NC && NC > 1) {
         // freed: oldB (sent left); top(P-1) moves to bottom(P-1); received: top from c-1
         for (int r = tid; r < m; r += nt) {
           Acol[(size_t)oldB * m_max + r] = Acol[(size_t)(RT0 + par) * m_max + r];
-          Vcol[(size_t)oldB * m_max + r] = Vcol[(size_t)(RT0 + par) * m_max + r];
+          if constexpr (!VG) Vcol[(size_t)oldB * m_max + r] = Vcol[(size_t)(RT0 + par) * m_max + r];
         }
         if (tid == 0) colid[oldB] = colid[RT0 + par];
       }
@@ -313,7 +322,8 @@ k_jacobi_cluster(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ 
     const double sg = ldexp(sqrt(nk), ex);
     if (!isfinite(sg) && status) atomicOr(status, DEV_NONFINITE);
     sigma[rank] = sg;
-    for (int r = 0; r < m; ++r) Vout[r + (size_t)rank * ldV] = Vcol[(size_t)slot * m_max + r];
+    for (int r = 0; r < m; ++r)
+      Vout[r + (size_t)rank * ldV] = VG ? Vg[r + (size_t)id * ldVg] : Vcol[(size_t)slot * m_max + r];
   }
   cl.sync();  // no CTA leaves while others may still read its shared memory
 }
@@ -590,23 +600,28 @@ k_jacobi_block(const RI* __restrict__ R, int64_t ldR, const int* __restrict__ m_
 }
 
 std::mutex g_cl_mu;
-int g_cl_ok[2][17];  // [type][NC]: 0 unknown, 1 usable, -1 not usable
+int g_cl_ok[2][2][17];  // [type][V in global][NC]: 0 unknown, 1 usable, -1 not usable
 
 }  // namespace
 
-size_t jacobi_cluster_smem(Fmt comp, int m_max, int npl) {
+size_t jacobi_cluster_smem(Fmt comp, int m_max, int npl, bool vg) {
   const int nslot = 2 * npl + 4;
   const int P2 = 2 * 16 * npl;  // allnorm holds up to MP doubles
-  return (size_t)2 * nslot * m_max * fmt_bytes(comp) + (size_t)((nslot + 1) & ~1) * 4 +
+  return (size_t)(vg ? 1 : 2) * nslot * m_max * fmt_bytes(comp) + (size_t)((nslot + 1) & ~1) * 4 +
          (size_t)P2 * sizeof(double) + 16;
 }
+// V in global memory where A and V together do not fit
+bool jacobi_cluster_vg(Fmt comp, int m_max, int npl) {
+  return jacobi_cluster_smem(comp, m_max, npl, false) > 200 * 1024;
+}
 
-// positions per CTA for a cluster of nc CTAs and this m (0 if it does not fit)
+// positions per CTA for a cluster of nc CTAs and this m (0 if it does not fit, even with
+// V in global memory)
 int jacobi_cluster_npl(Fmt comp, int m_max, int nc) {
   int npl = (m_max + 2 * nc - 1) / (2 * nc);
   if (npl < 2) npl = 2;
   if (npl > 64) return 0;
-  return jacobi_cluster_smem(comp, m_max, npl) <= 200 * 1024 ? npl : 0;
+  return jacobi_cluster_smem(comp, m_max, npl, jacobi_cluster_vg(comp, m_max, npl)) <= 200 * 1024 ? npl : 0;
 }
 
 // preferred cluster size for m (0 = use the single-CTA kernel); the caller falls back
@@ -624,12 +639,12 @@ int jacobi_cluster_plan(Fmt comp, int m_max, int* npl_out) {
   return 0;
 }
 
-template <class C, class RI, int G>
+template <class C, class RI, int G, bool VG>
 static cudaError_t launch_cl(const void* R, int64_t ldR, const int* m_dev, int m_max, int nc,
                              int npl, double* sigma, void* Vout, int ldV, int* status,
-                             int* sweeps_out, cudaStream_t s) {
-  auto k = k_jacobi_cluster<C, RI, G>;
-  const size_t smem = jacobi_cluster_smem(std::is_same<C, df>::value ? Fmt::DF : Fmt::F64, m_max, npl);
+                             int* sweeps_out, void* Vg, int ldVg, cudaStream_t s) {
+  auto k = k_jacobi_cluster<C, RI, G, VG>;
+  const size_t smem = jacobi_cluster_smem(std::is_same<C, df>::value ? Fmt::DF : Fmt::F64, m_max, npl, VG);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (nc > 8) {
@@ -654,7 +669,7 @@ static cudaError_t launch_cl(const void* R, int64_t ldR, const int* m_dev, int m
   // can a cluster of this size and shared memory be resident at all? (checked once)
   {
     std::lock_guard<std::mutex> lk(g_cl_mu);
-    int& ok = g_cl_ok[std::is_same<C, df>::value ? 0 : 1][nc];
+    int& ok = g_cl_ok[std::is_same<C, df>::value ? 0 : 1][VG ? 1 : 0][nc];
     if (ok == 0) {
       int nclusters = 0;
       ok = (cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg) == cudaSuccess && nclusters > 0) ? 1 : -1;
@@ -663,25 +678,28 @@ static cudaError_t launch_cl(const void* R, int64_t ldR, const int* m_dev, int m
     if (ok < 0) return cudaErrorNotSupported;
   }
   return cudaLaunchKernelEx(&cfg, k, static_cast<const RI*>(R), ldR, m_dev, m_max, npl, sigma,
-                            static_cast<C*>(Vout), ldV, status, sweeps_out, 60);
+                            static_cast<C*>(Vout), ldV, status, sweeps_out, 60, static_cast<C*>(Vg), ldVg);
 }
 
 cudaError_t launch_jacobi_cluster(Fmt comp, Fmt rin, const void* R, int64_t ldR, const int* m_dev,
                                   int m_max, int nc, int npl, double* sigma, void* Vout, int ldV,
-                                  int* status, int* sweeps_out, cudaStream_t s) {
+                                  int* status, int* sweeps_out, void* Vg, int ldVg, cudaStream_t s) {
   const bool wide = m_max > 128;
-  if (comp == Fmt::DF && rin == Fmt::DF)
-    return wide ? launch_cl<df, df, 32>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV, status, sweeps_out, s)
-                : launch_cl<df, df, 16>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV, status, sweeps_out, s);
-  if (comp == Fmt::DF && rin == Fmt::F32)
-    return wide ? launch_cl<df, float, 32>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV, status, sweeps_out, s)
-                : launch_cl<df, float, 16>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV, status, sweeps_out, s);
-  if (comp == Fmt::DF && rin == Fmt::F64)
-    return wide ? launch_cl<df, double, 32>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV, status, sweeps_out, s)
-                : launch_cl<df, double, 16>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV, status, sweeps_out, s);
-  if (comp == Fmt::F64 && rin == Fmt::F64)
-    return wide ? launch_cl<double, double, 32>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV, status, sweeps_out, s)
-                : launch_cl<double, double, 16>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV, status, sweeps_out, s);
+  // V in global memory (a scratch of ldVg x m_max) where A and V do not both fit
+  const bool vg = jacobi_cluster_vg(comp, m_max, npl);
+  if (vg && (!Vg || !wide || ldVg < m_max)) return cudaErrorInvalidValue;
+#define TT_CL(C, RI)                                                                               \
+  return vg ? launch_cl<C, RI, 32, true>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV, status,  \
+                                         sweeps_out, Vg, ldVg, s)                                  \
+         : wide ? launch_cl<C, RI, 32, false>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV,      \
+                                              status, sweeps_out, nullptr, 0, s)                   \
+                : launch_cl<C, RI, 16, false>(R, ldR, m_dev, m_max, nc, npl, sigma, Vout, ldV,      \
+                                              status, sweeps_out, nullptr, 0, s)
+  if (comp == Fmt::DF && rin == Fmt::DF) TT_CL(df, df);
+  if (comp == Fmt::DF && rin == Fmt::F32) TT_CL(df, float);
+  if (comp == Fmt::DF && rin == Fmt::F64) TT_CL(df, double);
+  if (comp == Fmt::F64 && rin == Fmt::F64) TT_CL(double, double);
+#undef TT_CL
   return cudaErrorInvalidValue;
 }
 

@@ -126,7 +126,7 @@ def test_tsqr_low_rank_wide_panels(m, rank):
     assert np.all(s[rank:] <= 1e-12 * s[0])
 
 
-@pytest.mark.parametrize("m", [1, 2, 3, 8, 17, 40, 64, 80, 131, 160, 257, 400])
+@pytest.mark.parametrize("m", [1, 2, 3, 8, 17, 40, 64, 80, 131, 160, 257, 400, 450, 512])
 def test_small_svd(m):
     rng = np.random.default_rng(m)
     R = np.triu(rng.standard_normal((m, m)))

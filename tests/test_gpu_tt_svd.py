@@ -150,6 +150,20 @@ def test_wide_step_beyond_shared_memory(dtype, arith):
     compare(X, res, ref, 1e-10 if dtype == torch.float64 else 1e-5)
 
 
+# an unfolding with m = 512 (n 8 x rank cap 64): its small SVD runs on a 16-CTA cluster with
+# V in global memory (A and V of 512 columns do not both fit the cluster's shared memory)
+@pytest.mark.parametrize("dtype,arith", [(torch.float64, "df"), (torch.float32, "df")])
+def test_m512_small_svd_with_global_v(dtype, arith):
+    dims = (8, 8, 8, 2, 8, 8, 3, 8)
+    X = planted_tt(dims, 24, seed=9, noise_rel=1e-3)
+    if dtype == torch.float32:
+        X = X.astype(np.float32).astype(np.float64)
+    res = run_gpu(X, 64, dtype=dtype, arith=arith)
+    ref = O.tt_svd(X, 64)
+    assert max(ref.ranks) == 64
+    compare(X, res, ref, 1e-10 if dtype == torch.float64 else 1e-5)
+
+
 def test_repeated_runs_are_identical():
     X = uniform_tensor((4,) * 10, seed=2)
     plan = api.TTSVDPlan(X.shape, 8, 0.0, torch.float64, "df", want_sigma=True)
