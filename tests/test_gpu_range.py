@@ -149,3 +149,18 @@ def test_tsqr_building_block_fp32_tiny():
     sig = np.linalg.svd(R, compute_uv=False)
     ref = np.linalg.svd(W.astype(np.float64), compute_uv=False)
     assert np.max(np.abs(sig - ref)) <= 2e-5 * ref[0]
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+@pytest.mark.parametrize("where", [0, 4000, 8 ** 5 - 1])
+@pytest.mark.parametrize("dtype,arith", [(torch.float64, "df"), (torch.float64, "f64"), (torch.float32, "df")])
+def test_non_finite_input_is_reported(bad, where, dtype, arith):
+    # a NaN or an infinity anywhere in X must surface as TT_ENUMERIC (a non-finite singular
+    # value), never as a finite result: the digit extraction of the tensor-core products
+    # reads exponent fields and could otherwise turn such a value into finite garbage
+    X = uniform_tensor((8,) * 5, seed=5)
+    Xf = X.ravel(order="F").copy()
+    Xf[where] = bad
+    plan = api.TTSVDPlan((8,) * 5, 10, 0.0, dtype, arith, want_sigma=True)
+    plan.run(torch.from_numpy(Xf).to("cuda", dtype))
+    assert plan.device_status() == api.capi.TT_ENUMERIC
