@@ -70,7 +70,7 @@ def parse():
     p.add_argument("--serve-only", action="store_true", help="only the serving leg (both admission orders)")
     p.add_argument("--case", default="", help="one building block for profiling instead of the bench: "
                    "tsqr:ROWS:M[:LAYOUT] (float-float TSQR of a uniform FP64 matrix), tsqr64:ROWS:M (native FP64), ttsvd32:N:D:RMAX (FP32 form), fma (ALU rate probes), "
-                   "tsmm:ROWS:M:K (W V(:, 0:K) of a uniform FP64 W) or svd:M (small SVD of a "
+                   "tsmm:ROWS:M:K (W V(:, 0:K) of a uniform FP64 W), tsmm64:ROWS:M:K (the same in native FP64) or svd:M (small SVD of a "
                    "uniform upper-triangular R) or ttsvd:N:D:RMAX:ARITH (a whole TT-SVD of a "
                    "uniform N^D FP64 tensor, ARITH f64 or df), each optionally followed by "
                    ":KEY=VALUE tuning keys; prints one JSON line")
@@ -284,6 +284,17 @@ def run_case(spec: str) -> int:
         Y = torch.empty(rows * k, dtype=torch.float64, device="cuda")
         call = lambda: capi.tt_tsmm(W.data_ptr(), capi.TT_F64, rows, m, rows, V.data_ptr(), k,
                                     Y.data_ptr(), rows, int(s.cuda_stream))
+    elif parts[0] == "tsmm64":
+        # tsmm64:ROWS:M:K -- the native FP64 form's W V(:, 0:K) (tt_tsmm_ex)
+        rows, m, k = int(parts[1]), int(parts[2]), int(parts[3])
+        W = api.gen_uniform(rows * m, 3, torch.float64)
+        import numpy as np
+        Vh = np.linalg.qr(np.random.default_rng(0).standard_normal((m, m)))[0]
+        V = torch.from_numpy(np.asfortranarray(Vh).ravel(order="F").copy()).cuda()
+        Y = torch.empty(rows * k, dtype=torch.float64, device="cuda")
+        call = lambda: capi.check(capi.lib().tt_tsmm_ex(W.data_ptr(), capi.TT_F64, rows, m, rows, V.data_ptr(), k,
+                                                        Y.data_ptr(), rows, capi.TT_ARITH_F64,
+                                                        int(s.cuda_stream)), "tt_tsmm_ex")
     elif parts[0] == "ttsvd":
         # ttsvd:N:D:RMAX:ARITH -- a whole TT-SVD of a uniform N^D FP64 tensor
         n, d, r, ar = int(parts[1]), int(parts[2]), int(parts[3]), parts[4]

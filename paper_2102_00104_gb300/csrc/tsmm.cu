@@ -253,6 +253,17 @@ TsmmCfg plan_tsmm(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max, int
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (c.smem + 1024)));
     const int64_t ntiles = (rows + 63) / 64;
     c.ctas = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)nsm * per_sm));
+    // the native FP64 form: the tcgen05 pipeline where it applies, this launch as its
+    // fallback (a W whose tensor map cannot be made)
+    if (tsmm_ws_ok(in, comp, vfmt, out, m_max, r_max) && rows >= 128) {
+      c.fb_rc = c.rc;
+      c.fb_smem = c.smem;
+      c.fb_ctas = c.ctas;
+      c.kind = 4;
+      c.tr = 128;
+      c.smem = tsmm_ws_smem(m_max);
+      c.ctas = std::max<int64_t>(1, std::min<int64_t>((rows + 127) / 128, (int64_t)nsm));
+    }
     return c;
   }
   // register-blocked form when V(:, 0:r) fits in shared memory
@@ -296,6 +307,18 @@ cudaError_t launch_tsmm(const TsmmCfg& c, const void* W, int64_t rows, int64_t l
                         int64_t ldy, int* status, cudaStream_t s) {
   if (c.kind == 3) return launch_tsmm_tc(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
   if (c.kind == 2) return launch_tsmm_oz(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+  if (c.kind == 4) {
+    bool used = false;
+    const cudaError_t e = launch_tsmm_ws(c, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s, &used);
+    if (used || e != cudaSuccess) return e;
+    TsmmCfg o = c;
+    o.kind = 2;
+    o.tr = 64;
+    o.rc = c.fb_rc;
+    o.smem = c.fb_smem;
+    o.ctas = c.fb_ctas;
+    return launch_tsmm_oz(o, W, rows, ld, m_dev, V, ldV, r_dev, Y, ldy, status, s);
+  }
 #define TT_TSMM(IN, CO, VF, OUT)                                                                \
   if (c.in == Fmt::IN && c.comp == Fmt::CO && c.vfmt == Fmt::VF && c.out == Fmt::OUT)           \
     return run<T_<Fmt::CO>, T_<Fmt::IN>, T_<Fmt::VF>, T_<Fmt::OUT>>(c, W, rows, ld, m_dev, V, ldV, \
