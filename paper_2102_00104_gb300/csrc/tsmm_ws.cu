@@ -2,10 +2,11 @@
 // native FP64 form on the fifth-generation tensor cores, as a warp-specialised pipeline:
 //
 //   TMA warp     cp.async.bulk.tensor.2d loads 128-row tiles of W (column-major FP64) into
-//                two shared-memory stages;
+//                three shared-memory stages;
 //   digit warps  (eight: two per 32-row quarter, each taking half of a row's k range) turn
 //                a tile into seven FP16 digit planes, one k-step (16 columns) at a time,
-//                into two digit slots in the canonical K-major layout of tcgen05.mma;
+//                and store them with tcgen05.st into one of four digit slots in tensor
+//                memory (lane = row, two k per 32-bit column), the A operand of the MMAs;
 //   MMA thread   issues, per k-step, one tcgen05.mma.kind::f16 per digit a of W against
 //                V's digits 0..6-a stacked along N, accumulating every digit product of
 //                one level a + b into the same block of tensor memory (two accumulator
@@ -53,13 +54,17 @@ constexpr int WS_ND = 7;          // digits per value
 constexpr int WS_KT = WS_MAXM / 16;
 constexpr int WS_WARPS = 14;      // 0-3 epilogue, 4-11 digits, 12 TMA, 13 MMA
 constexpr int WS_THREADS = 32 * WS_WARPS;
-constexpr uint32_t WS_TMCOLS = 256;  // two accumulator buffers of 128 columns
-constexpr int WS_APLANE = WS_TR * 16 * 2;        // one digit plane of a k-step: 4 KB
-constexpr int WS_ASLOT = WS_ND * WS_APLANE;      // 28 KB
+constexpr int WS_NWS = 3;         // W stages
+constexpr int WS_NDS = 4;         // digit slots
+constexpr int WS_NER = 8;         // row-exponent ring (tiles)
+// tensor memory: accumulator buffers at columns 0 and 128 (7 x 16 used), digit slot s at
+// 256 + 64 s (digit a of a k-step in columns 8a .. 8a+7: sixteen FP16 k per lane)
+constexpr uint32_t WS_TMCOLS = 512;
+constexpr uint32_t WS_TM_A = 256;
 
 struct WsBars {
-  uint64_t wfull[2], wempty[2];   // W stages: TMA landed / digit warps done reading
-  uint64_t dfull[2], dempty[2];   // digit slots: written / MMAs done reading
+  uint64_t wfull[WS_NWS], wempty[WS_NWS];   // W stages: TMA landed / digit warps done reading
+  uint64_t dfull[WS_NDS], dempty[WS_NDS];   // digit slots: written / MMAs done reading
   uint64_t afull[2], aempty[2];   // accumulators: products ready / read back
   uint64_t xch[4];                // row-maximum exchange of the two digit warps of a quarter
   uint64_t done;                  // the MMA thread's final drain
@@ -67,16 +72,15 @@ struct WsBars {
   int abort_flag;
 };
 
-// dynamic shared memory: W stages, digit slots, V's digit planes, then the small arrays
-__host__ __device__ constexpr size_t ws_off_a(int m_max) { return 2 * (size_t)WS_TR * m_max * 8; }
-__host__ __device__ constexpr size_t ws_off_b(int m_max) { return ws_off_a(m_max) + 2 * (size_t)WS_ASLOT; }
+// dynamic shared memory: W stages, V's digit planes, then the small arrays
+__host__ __device__ constexpr size_t ws_off_b(int m_max) { return WS_NWS * (size_t)WS_TR * m_max * 8; }
 __host__ __device__ constexpr size_t ws_bplane(int kt) { return (size_t)WS_NN * 32 * kt; }
 __host__ __device__ constexpr size_t ws_off_small(int m_max) {
   return ws_off_b(m_max) + WS_ND * ws_bplane((m_max + 15) / 16);
 }
 __host__ __device__ constexpr size_t ws_smem(int m_max) {
-  // Erow[4][128], Xch[2][2][128], Fe[16] ints, then the barriers
-  return ws_off_small(m_max) + (4 * WS_TR + 4 * WS_TR + WS_NN) * sizeof(int) + sizeof(WsBars) + 64;
+  // Erow[WS_NER][128], Xch[2][2][128], Fe[16] ints, then the barriers
+  return ws_off_small(m_max) + (WS_NER * WS_TR + 4 * WS_TR + WS_NN) * sizeof(int) + sizeof(WsBars) + 64;
 }
 
 __device__ __forceinline__ void ws_bar_init(uint64_t* b, uint32_t count) {
@@ -129,12 +133,18 @@ __device__ __forceinline__ uint64_t ws_desc(uint32_t addr, uint32_t sbo) {
 __host__ __device__ constexpr uint32_t ws_idesc(int nn) {
   return (1u << 4) | ((uint32_t)(nn >> 3) << 17) | ((128u >> 4) << 24);
 }
-__device__ __forceinline__ void ws_mma(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+// D (tensor memory) += A (tensor memory) B (shared memory descriptor)
+__device__ __forceinline__ void ws_mma(uint32_t dtm, uint32_t atm, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(dtm),
+      "r"(atm), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
+}
+__device__ __forceinline__ void ws_st4(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(a), "r"(b),
+               "r"(c), "r"(d)
+               : "memory");
 }
 __device__ __forceinline__ void ws_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
@@ -281,21 +291,24 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
   }
   const int kt = (m_max + 15) / 16;
   const size_t wstage = (size_t)WS_TR * m_max * 8;
-  unsigned char* Wst = smem_raw;                   // two stages, column-major 128 x m_max
-  unsigned char* Ad = smem_raw + ws_off_a(m_max);  // two digit slots (seven planes each)
+  unsigned char* Wst = smem_raw;                   // W stages, column-major 128 x m_max
   unsigned char* Bd = smem_raw + ws_off_b(m_max);  // V's seven digit planes
-  int* Erow = reinterpret_cast<int*>(smem_raw + ws_off_small(m_max));  // [4][128]
-  int* Xch = Erow + 4 * WS_TR;                                         // [2][2][128]
+  int* Erow = reinterpret_cast<int*>(smem_raw + ws_off_small(m_max));  // [WS_NER][128]
+  int* Xch = Erow + WS_NER * WS_TR;                                    // [2][2][128]
   int* Fe = Xch + 4 * WS_TR;                                           // [16]
   WsBars& B = *reinterpret_cast<WsBars*>(Fe + WS_NN);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < WS_NWS; ++s) {
       ws_bar_init(&B.wfull[s], 1);
       ws_bar_init(&B.wempty[s], 8);
+    }
+    for (int s = 0; s < WS_NDS; ++s) {
       ws_bar_init(&B.dfull[s], 8);
       ws_bar_init(&B.dempty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
       ws_bar_init(&B.afull[s], 2);
       ws_bar_init(&B.aempty[s], 4);
     }
@@ -346,19 +359,19 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
   const int64_t ntiles = (rows + WS_TR - 1) / WS_TR;
 
   if (warp == 12) {
-    // ---- TMA: tile n of this CTA into stage n mod 2 --------------------------------------
+    // ---- TMA: tile n of this CTA into stage n mod WS_NWS ---------------------------------
     if (lane == 0) {
       int n = 0;
       for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++n) {
-        const int st = n & 1;
-        if (!ws_wait(&B.wempty[st], ((n >> 1) & 1) ^ 1, &B.abort_flag)) break;
+        const int st = n % WS_NWS;
+        if (!ws_wait(&B.wempty[st], ((n / WS_NWS) & 1) ^ 1, &B.abort_flag)) break;
         oz_expect(&B.wfull[st], (uint32_t)wstage);
         ws_tma_2d(Wst + st * wstage, &tmW, (int)(t * WS_TR), 0, &B.wfull[st]);
       }
       // the copies in flight land before the CTA leaves: the last use u of stage s
-      for (int s = 0; s < 2 && s < n; ++s) {
-        const int u = s + 2 * ((n - 1 - s) >> 1);
-        ws_drain(&B.wfull[s], (uint32_t)((u >> 1) & 1));
+      for (int s = 0; s < WS_NWS && s < n; ++s) {
+        const int u = s + WS_NWS * ((n - 1 - s) / WS_NWS);
+        ws_drain(&B.wfull[s], (uint32_t)((u / WS_NWS) & 1));
       }
     }
     __syncwarp();
@@ -368,8 +381,8 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
     int n = 0, kc = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++n) {
-      const int st = n & 1;
-      if (!ws_wait(&B.wfull[st], (n >> 1) & 1, &B.abort_flag)) break;
+      const int st = n % WS_NWS;
+      if (!ws_wait(&B.wfull[st], (n / WS_NWS) & 1, &B.abort_flag)) break;
       const double* Wt = reinterpret_cast<const double*>(Wst + st * wstage);
       double x[WS_KT][8];
       uint32_t em = 0;
@@ -393,20 +406,22 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
 #pragma unroll
       for (int kk = 0; kk < WS_KT; ++kk) {
         if (kk >= kt) break;
-        const int slot = kc & 1;
-        if (!ws_wait(&B.dempty[slot], ((kc >> 1) & 1) ^ 1, &B.abort_flag)) {
+        const int slot = kc % WS_NDS;
+        if (!ws_wait(&B.dempty[slot], ((kc / WS_NDS) & 1) ^ 1, &B.abort_flag)) {
           ok = false;
           break;
         }
-        // (after the slot wait: the epilogue of the tile four back has read this entry)
-        if (kk == 0 && h == 0) Erow[(n & 3) * WS_TR + i] = Eb;
+        ws_fence_after();
+        // (after the slot wait: the MMAs of a k-step WS_NDS back have completed, so the
+        // epilogue is past the tile WS_NDS + 2 back, the entry's previous reader)
+        if (kk == 0 && h == 0) Erow[(n % WS_NER) * WS_TR + i] = Eb;
         uint32_t dd[4][WS_ND];
         ws_digits8(x[kk], Eb, dd);
-        unsigned char* As = Ad + slot * WS_ASLOT + (i >> 3) * 256 + h * 128 + (i & 7) * 16;
+        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + WS_TM_A + 64u * slot + 4u * h;
 #pragma unroll
-        for (int a = 0; a < WS_ND; ++a)
-          *reinterpret_cast<uint4*>(As + a * WS_APLANE) = make_uint4(dd[0][a], dd[1][a], dd[2][a], dd[3][a]);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int a = 0; a < WS_ND; ++a) ws_st4(ta + 8u * a, dd[0][a], dd[1][a], dd[2][a], dd[3][a]);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        ws_fence_before();
         __syncwarp();
         if (lane == 0) ws_arrive(&B.dfull[slot]);
         ++kc;
@@ -415,7 +430,7 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
   } else if (warp == 13) {
     // ---- MMA issue: the 7 digit products of each k-step into accumulator n mod 2 ---------
     if (lane == 0) {
-      const uint32_t a0 = smem_u32(Ad), b0 = smem_u32(Bd);
+      const uint32_t b0 = smem_u32(Bd);
       int n = 0, kc = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++n) {
@@ -423,8 +438,8 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
         if (!ws_wait(&B.aempty[acc], ((n >> 1) & 1) ^ 1, &B.abort_flag)) break;
         ws_fence_after();
         for (int kk = 0; kk < kt; ++kk) {
-          const int slot = kc & 1;
-          if (!ws_wait(&B.dfull[slot], (kc >> 1) & 1, &B.abort_flag)) {
+          const int slot = kc % WS_NDS;
+          if (!ws_wait(&B.dfull[slot], (kc / WS_NDS) & 1, &B.abort_flag)) {
             ok = false;
             break;
           }
@@ -432,8 +447,7 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
           const uint64_t bd = ws_desc(b0 + 256u * kk, 256u * kt);
 #pragma unroll
           for (int a = 0; a < WS_ND; ++a)
-            ws_mma(tmem + (uint32_t)(acc * 128 + 16 * a),
-                   ws_desc(a0 + (uint32_t)(slot * WS_ASLOT + a * WS_APLANE), 256u), bd,
+            ws_mma(tmem + (uint32_t)(acc * 128 + 16 * a), tmem + WS_TM_A + 64u * slot + 8u * a, bd,
                    ws_idesc(16 * (WS_ND - a)), (kk | a) ? 1u : 0u);
           ws_commit(&B.dempty[slot]);
           ++kc;
@@ -455,7 +469,7 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
       const int acc = n & 1;
       if (!ws_wait(&B.afull[acc], (n >> 1) & 1, &B.abort_flag)) break;
       ws_fence_after();
-      const int Eb = Erow[(n & 3) * WS_TR + i];
+      const int Eb = Erow[(n % WS_NER) * WS_TR + i];
       const int64_t row = t * WS_TR + i;
       const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * 128);
       for (int half = 0; half < 2; ++half) {
