@@ -79,8 +79,8 @@ __host__ __device__ constexpr size_t ws_off_small(int m_max) {
   return ws_off_b(m_max) + WS_ND * ws_bplane((m_max + 15) / 16);
 }
 __host__ __device__ constexpr size_t ws_smem(int m_max) {
-  // Erow[WS_NER][128], Xch[2][2][128], Fe[16] ints, then the barriers
-  return ws_off_small(m_max) + (WS_NER * WS_TR + 4 * WS_TR + WS_NN) * sizeof(int) + sizeof(WsBars) + 64;
+  // Erow[WS_NER][128], Xch[2][2][2][128], Fe[16] ints, then the barriers
+  return ws_off_small(m_max) + (WS_NER * WS_TR + 8 * WS_TR + WS_NN) * sizeof(int) + sizeof(WsBars) + 64;
 }
 
 __device__ __forceinline__ void ws_bar_init(uint64_t* b, uint32_t count) {
@@ -163,13 +163,14 @@ __device__ __forceinline__ void ws_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr));
 }
 
-// v + C of an FP64 value of a row (or column) with scale exponent Eb >= 1 (ws_scale_exp):
-// v = x 2^(1085 - Eb) as a 64-bit two's-complement integer (|v| < 2^63 - 2^55), C =
-// 0x8080808080808080, returned as two words.  FAST (Eb >= 56): every entry is read with the
+// |v| + C of an FP64 value of a row (or column) with scale exponent Eb >= 1 (ws_scale_exp):
+// |v| = |x| 2^(1085 - Eb) as a 64-bit integer (below 2^63 - 2^55), C = 0x8080808080808080,
+// returned as two words.  The sign of x is applied to the digits afterwards: the balanced
+// digits of -|v| are those of |v| negated.  FAST (Eb >= 56): every entry is read with the
 // implicit bit, which for a zero or subnormal entry leaves a value below 2^7 that the
-// dropped byte absorbs (without carry or borrow); otherwise zero and subnormal entries are
-// decoded exactly.
-template <bool FAST>
+// dropped byte absorbs (without carry); otherwise zero and subnormal entries are decoded
+// exactly.  NEAR (every entry of the row has Eb - max(e, 1) <= 31): one funnel shift.
+template <bool FAST, bool NEAR>
 __device__ __forceinline__ void ws_fix(double x, int Eb, uint32_t& wh, uint32_t& wl) {
   const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
   const int e = (int)((hi >> 20) & 0x7FFu);
@@ -182,68 +183,83 @@ __device__ __forceinline__ void ws_fix(double x, int Eb, uint32_t& wh, uint32_t&
     mh = (hi & 0xFFFFFu) | (e ? 0x100000u : 0u);
     d = Eb - max(e, 1);
   }
-  // (M << 10) >> d with d >= 0: a funnel shift by min(d, 32), then by max(d - 32, 0)
+  // (M << 10) >> d with d >= 0
   const uint32_t h9 = __funnelshift_l(lo, mh, 10), l9 = lo << 10;
-  const uint32_t l1 = __funnelshift_rc(l9, h9, (uint32_t)d);
-  const uint32_t h1 = __funnelshift_rc(h9, 0u, (uint32_t)d);
-  const uint32_t l2 = __funnelshift_rc(l1, h1, (uint32_t)max(d - 32, 0));
-  // negative x: -v = ~v + 1, so w = (v ^ s) + C + (s & 1) with s the sign mask
-  const uint32_t sm = (uint32_t)((int)hi >> 31);
-  const uint64_t v = ((uint64_t)(h1 ^ sm) << 32) | (uint64_t)(l2 ^ sm);
-  const uint64_t w = v + 0x8080808080808080ull + (uint64_t)(hi >> 31);
+  uint32_t h1, l2;
+  if (NEAR) {
+    l2 = __funnelshift_r(l9, h9, (uint32_t)d);
+    h1 = h9 >> d;
+  } else {
+    // a funnel shift by min(d, 32), then by max(d - 32, 0)
+    const uint32_t l1 = __funnelshift_rc(l9, h9, (uint32_t)d);
+    h1 = __funnelshift_rc(h9, 0u, (uint32_t)d);
+    l2 = __funnelshift_rc(l1, h1, (uint32_t)max(d - 32, 0));
+  }
+  const uint64_t w = (((uint64_t)h1 << 32) | (uint64_t)l2) + 0x8080808080808080ull;
   wh = (uint32_t)(w >> 32);
   wl = (uint32_t)w;
 }
 
-// FP16 pair (1024 + b_x, 1024 + b_y) - 1152 = (b_x - 128, b_y - 128), exactly
-__device__ __forceinline__ uint32_t ws_h2(uint32_t pr) {
+// FP16 pair s (1024 + b) - 1152 s = s (b - 128) for the signs s = +-1 of x (low half) and y
+// (high half), exactly; S holds (s_x, s_y), T = -1152 S
+__device__ __forceinline__ uint32_t ws_h2(uint32_t pr, uint32_t S, uint32_t T) {
   uint32_t o;
-  asm("add.rn.f16x2 %0, %1, %2;" : "=r"(o) : "r"(pr), "r"(0xE480E480u));
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(o) : "r"(pr), "r"(S), "r"(T));
   return o;
 }
-// the seven digits of two values x (low half) and y (high half) from their words v + C:
-// digit a is byte 7 - a, less 128
-__device__ __forceinline__ void ws_digits(uint32_t xh, uint32_t xl, uint32_t yh, uint32_t yl,
-                                          uint32_t (&d)[WS_ND]) {
+// the seven digits of two values x (low half) and y (high half) from their words |v| + C
+// and the high words of x and y (their signs): digit a is byte 7 - a, less 128, times the
+// value's sign
+__device__ __forceinline__ void ws_digits(uint32_t xh, uint32_t xl, uint32_t yh, uint32_t yl, uint32_t xs,
+                                          uint32_t ys, uint32_t (&d)[WS_ND]) {
   constexpr uint32_t K = 0x64646464u;  // FP16 exponent byte of 1024
+  const uint32_t sp = __byte_perm(xs, ys, 0x7030) & 0x80008000u;
+  const uint32_t S = sp | 0x3C003C00u, T = sp ^ 0xE480E480u;
   const uint32_t H1 = __byte_perm(xh, yh, 0x5140), H2 = __byte_perm(xh, yh, 0x7362);
   const uint32_t L1 = __byte_perm(xl, yl, 0x5140), L2 = __byte_perm(xl, yl, 0x7362);
-  d[0] = ws_h2(__byte_perm(H2, K, 0x4342));
-  d[1] = ws_h2(__byte_perm(H2, K, 0x4140));
-  d[2] = ws_h2(__byte_perm(H1, K, 0x4342));
-  d[3] = ws_h2(__byte_perm(H1, K, 0x4140));
-  d[4] = ws_h2(__byte_perm(L2, K, 0x4342));
-  d[5] = ws_h2(__byte_perm(L2, K, 0x4140));
-  d[6] = ws_h2(__byte_perm(L1, K, 0x4342));
+  d[0] = ws_h2(__byte_perm(H2, K, 0x4342), S, T);
+  d[1] = ws_h2(__byte_perm(H2, K, 0x4140), S, T);
+  d[2] = ws_h2(__byte_perm(H1, K, 0x4342), S, T);
+  d[3] = ws_h2(__byte_perm(H1, K, 0x4140), S, T);
+  d[4] = ws_h2(__byte_perm(L2, K, 0x4342), S, T);
+  d[5] = ws_h2(__byte_perm(L2, K, 0x4140), S, T);
+  d[6] = ws_h2(__byte_perm(L1, K, 0x4342), S, T);
 }
 // scale exponent of a row (or column) from the largest of its entries' high words
 // (sign cleared): the largest exponent field, plus one where the mantissa's top 20 bits
-// reach 0xFDFDF (so that v = x 2^(1085 - Eb) stays below 2^64 - C); at least 1; kWsNonfinite
-// where the row holds an infinity or a NaN (its digits are then all zero)
+// reach 0xFDFDF (so that |v| = |x| 2^(1085 - Eb) stays below 2^64 - C); at least 1;
+// kWsNonfinite where the row holds an infinity or a NaN (its digits are then all zero)
 constexpr int kWsNonfinite = 4096;
 __device__ __forceinline__ int ws_scale_exp(uint32_t mx) {
   if ((mx >> 20) == 0x7FFu) return kWsNonfinite;
   return max((int)(mx >> 20) + ((mx & 0xFFFFFu) >= 0xFDFDFu ? 1 : 0), 1);
 }
-// digits of eight consecutive k of one row (or column), as one 16-byte row of a core
-// matrix per plane
-__device__ __forceinline__ void ws_digits8(const double (&x)[8], int Eb, uint32_t (&dd)[4][WS_ND]) {
+template <bool FAST, bool NEAR>
+__device__ __forceinline__ void ws_digits8_(const double (&x)[8], int Eb, uint32_t (&dd)[4][WS_ND]) {
   uint32_t wh[8], wl[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) ws_fix<FAST, NEAR>(x[c], Eb, wh[c], wl[c]);
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+    ws_digits(wh[2 * p], wl[2 * p], wh[2 * p + 1], wl[2 * p + 1], (uint32_t)__double2hiint(x[2 * p]),
+              (uint32_t)__double2hiint(x[2 * p + 1]), dd[p]);
+}
+// digits of eight consecutive k of one row (or column), one 16-byte row of a core matrix
+// per plane; near: every entry of the row is within 2^31 of the scale (ws_fix)
+__device__ __forceinline__ void ws_digits8(const double (&x)[8], int Eb, bool near, uint32_t (&dd)[4][WS_ND]) {
   if (Eb >= 56) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) ws_fix<true>(x[c], Eb, wh[c], wl[c]);
+    if (near) ws_digits8_<true, true>(x, Eb, dd);
+    else ws_digits8_<true, false>(x, Eb, dd);
   } else {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) ws_fix<false>(x[c], Eb, wh[c], wl[c]);
+    if (near) ws_digits8_<false, true>(x, Eb, dd);
+    else ws_digits8_<false, false>(x, Eb, dd);
   }
-#pragma unroll
-  for (int p = 0; p < 4; ++p) ws_digits(wh[2 * p], wl[2 * p], wh[2 * p + 1], wl[2 * p + 1], dd[p]);
 }
 
 // Y_ij from the seven exact level sums (FP32 integers) of one output:
 // U = sum_L acc_L 2^(38 - 8L) (the part below 2^-10 of level 6 rounded off) as a 64-bit
-// integer, Y = U 2^(Eb + Fb - 2096), rounded to nearest by integer operations; NaN where
-// the row or the column held a non-finite value
+// integer, Y = U 2^(Eb + Fb - 2096) rounded to nearest (by integer operations where the
+// result leaves the normal range); NaN where the row or the column held a non-finite value
 __device__ __forceinline__ double ws_combine(const uint32_t (&v)[WS_ND][8], int c, int Eb, int Fb, int sh) {
   if (Eb == kWsNonfinite || Fb == kWsNonfinite) return __longlong_as_double(0x7FF8000000000000ll);
   int l[WS_ND];
@@ -252,6 +268,10 @@ __device__ __forceinline__ double ws_combine(const uint32_t (&v)[WS_ND][8], int 
   const long long shi = (long long)(l[0] * 256 + l[1]) * 65536 + (long long)(l[2] * 256 + l[3]);
   const long long slo = (long long)l[4] * 65536 + (long long)(l[5] * 256 + l[6]);
   const long long U = shi * 16384 + ((slo + 512) >> 10);
+  const int X = Eb + Fb - 2096 - sh;
+  // |U| < 2^58: for 2^-1022 <= 2^X <= 2^966 the result is normal, rounded once (U to FP64;
+  // the power of two is exact)
+  if (X >= -1022 && X <= 966) return __ll2double_rn(U) * __longlong_as_double((long long)(X + 1023) << 52);
   if (U == 0) return 0.0;
   const unsigned long long A = U < 0 ? (unsigned long long)(-U) : (unsigned long long)U;
   const int lz = __clzll((long long)A);
@@ -294,8 +314,8 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
   unsigned char* Wst = smem_raw;                   // W stages, column-major 128 x m_max
   unsigned char* Bd = smem_raw + ws_off_b(m_max);  // V's seven digit planes
   int* Erow = reinterpret_cast<int*>(smem_raw + ws_off_small(m_max));  // [WS_NER][128]
-  int* Xch = Erow + WS_NER * WS_TR;                                    // [2][2][128]
-  int* Fe = Xch + 4 * WS_TR;                                           // [16]
+  int* Xch = Erow + WS_NER * WS_TR;  // [tile parity][k-half][largest, smallest][128]
+  int* Fe = Xch + 8 * WS_TR;                                           // [16]
   WsBars& B = *reinterpret_cast<WsBars*>(Fe + WS_NN);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -345,7 +365,7 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
       x[c] = (n < r && k < m) ? V[k + (size_t)n * ldV] : 0.0;
     }
     uint32_t dd[4][WS_ND];
-    ws_digits8(x, Fe[n], dd);
+    ws_digits8(x, Fe[n], false, dd);
     const size_t off = (size_t)(n >> 3) * 256 * kt + (size_t)kg * 128 + (size_t)(n & 7) * 16;
 #pragma unroll
     for (int b = 0; b < WS_ND; ++b)
@@ -385,24 +405,30 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
       if (!ws_wait(&B.wfull[st], (n / WS_NWS) & 1, &B.abort_flag)) break;
       const double* Wt = reinterpret_cast<const double*>(Wst + st * wstage);
       double x[WS_KT][8];
-      uint32_t em = 0;
+      uint32_t em = 0, en = 0x7FFFFFFFu;
 #pragma unroll
       for (int kk = 0; kk < WS_KT; ++kk)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const int k = 16 * kk + 8 * h + c;
           x[kk][c] = (kk < kt && k < m) ? Wt[(size_t)k * WS_TR + i] : 0.0;
-          em = max(em, (uint32_t)__double2hiint(x[kk][c]) & 0x7FFFFFFFu);
+          const uint32_t a = (uint32_t)__double2hiint(x[kk][c]) & 0x7FFFFFFFu;
+          em = max(em, a);
+          en = min(en, a);
         }
       // the stage is read: back to the TMA warp
       __syncwarp();
       if (lane == 0) ws_arrive(&B.wempty[st]);
-      // the row's largest high word, with the other k-half's
-      Xch[((n & 1) * 2 + h) * WS_TR + i] = (int)em;
+      // the row's largest and smallest high words, with the other k-half's
+      Xch[((n & 1) * 4 + 2 * h) * WS_TR + i] = (int)em;
+      Xch[((n & 1) * 4 + 2 * h + 1) * WS_TR + i] = (int)en;
       __syncwarp();
       if (lane == 0) ws_arrive(&B.xch[q]);
       if (!ws_wait(&B.xch[q], n & 1, &B.abort_flag)) break;
-      const int Eb = ws_scale_exp(max(em, (uint32_t)Xch[((n & 1) * 2 + (h ^ 1)) * WS_TR + i]));
+      em = max(em, (uint32_t)Xch[((n & 1) * 4 + 2 * (h ^ 1)) * WS_TR + i]);
+      en = min(en, (uint32_t)Xch[((n & 1) * 4 + 2 * (h ^ 1) + 1) * WS_TR + i]);
+      const int Eb = ws_scale_exp(em);
+      const bool near = Eb - max((int)(en >> 20), 1) <= 31;
 #pragma unroll
       for (int kk = 0; kk < WS_KT; ++kk) {
         if (kk >= kt) break;
@@ -416,7 +442,7 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
         // epilogue is past the tile WS_NDS + 2 back, the entry's previous reader)
         if (kk == 0 && h == 0) Erow[(n % WS_NER) * WS_TR + i] = Eb;
         uint32_t dd[4][WS_ND];
-        ws_digits8(x[kk], Eb, dd);
+        ws_digits8(x[kk], Eb, near, dd);
         const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + WS_TM_A + 64u * slot + 4u * h;
 #pragma unroll
         for (int a = 0; a < WS_ND; ++a) ws_st4(ta + 8u * a, dd[0][a], dd[1][a], dd[2][a], dd[3][a]);
