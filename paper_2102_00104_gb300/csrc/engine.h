@@ -219,8 +219,8 @@ cudaError_t launch_finish(const DevState* st, int d, int64_t* ranks_out, double*
 struct TsmmCfg {
   int kind;         // 0 = shared-memory tile of W, 1 = register-blocked (V in shared memory),
                     // 2 = tensor cores, Ozaki splitting (float-float form), mma.sync,
-                    // 3 = the same on tcgen05, 4 = the native FP64 form's warp-specialised
-                    // tcgen05 pipeline (tsmm_ws.cu; kind 2 where W cannot be mapped)
+                    // 3 = the same on tcgen05, 4 = the warp-specialised tcgen05 pipeline
+                    // for an FP64 W (tsmm_ws.cu; kind 2 where W cannot be mapped)
   int cpt;          // kind 1: output columns per thread and pass
   Fmt in, comp, vfmt, out;
   int m_max, r_max;
@@ -249,7 +249,7 @@ size_t tsmm_tc_smem(int m_max, int r_max);
 cudaError_t launch_tsmm_tc(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,
                            const int* m_dev, const void* V, int ldV, const int* r_dev, void* Y,
                            int64_t ldy, int* status, cudaStream_t s);
-// the native FP64 form on a warp-specialised tcgen05 pipeline with TMA tile loads (tsmm_ws.cu)
+// an FP64 W on a warp-specialised tcgen05 pipeline with TMA tile loads (tsmm_ws.cu)
 bool tsmm_ws_ok(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max);
 size_t tsmm_ws_smem(int m_max);
 cudaError_t launch_tsmm_ws(const TsmmCfg& c, const void* W, int64_t rows, int64_t ld,

@@ -1,5 +1,6 @@
-// tsmm_ws.cu -- Y = W V(:, 0:r) of Alg. 2 (the W V_r step, TSMM of Sec. 4.1.2) for the
-// native FP64 form on the fifth-generation tensor cores, as a warp-specialised pipeline:
+// tsmm_ws.cu -- Y = W V(:, 0:r) of Alg. 2 (the W V_r step, TSMM of Sec. 4.1.2) for an FP64 W
+// (the native FP64 form's products, and the float-float form's first product, whose W is
+// the input X) on the fifth-generation tensor cores, as a warp-specialised pipeline:
 //
 //   TMA warp     cp.async.bulk.tensor.2d loads 128-row tiles of W (column-major FP64) into
 //                three shared-memory stages;
@@ -96,6 +97,7 @@ __device__ __forceinline__ bool ws_wait(uint64_t* b, uint32_t parity, int* abort
   if (oz_try(b, parity)) return true;
   const long long t0 = clock64();
   while (!oz_try(b, parity)) {
+    __nanosleep(256);  // a waiting role leaves its issue slots to the digit warps
     if (*reinterpret_cast<volatile int*>(abort_flag)) return false;
     if (clock64() - t0 > kWaitCycles) {
       *reinterpret_cast<volatile int*>(abort_flag) = 1;
@@ -293,13 +295,50 @@ __device__ __forceinline__ double ws_combine(const uint32_t (&v)[WS_ND][8], int 
   return __longlong_as_double((long long)(bits | sgn));
 }
 
+// V read as FP64 (a float-float value as the FP64 sum of its words: 53 bits of its ~48)
+__device__ __forceinline__ double ws_f64(double v) { return v; }
+__device__ __forceinline__ double ws_f64(df v) { return (double)v.hi + (double)v.lo; }
+// one output in the format of Y: FP64, or float-float (the top 48 bits of the integer U
+// turned into an FP32 pair by two exact conversions and a two-sum, then scaled by 2^X;
+// through FP64 where 2^X leaves FP32's range)
+template <class VT>
+__device__ __forceinline__ VT ws_out(const uint32_t (&v)[WS_ND][8], int c, int Eb, int Fb, int sh);
+template <>
+__device__ __forceinline__ double ws_out<double>(const uint32_t (&v)[WS_ND][8], int c, int Eb, int Fb, int sh) {
+  return ws_combine(v, c, Eb, Fb, sh);
+}
+template <>
+__device__ __forceinline__ df ws_out<df>(const uint32_t (&v)[WS_ND][8], int c, int Eb, int Fb, int sh) {
+  const int X = Eb + Fb - 2096 - sh;
+  if (Eb != kWsNonfinite && Fb != kWsNonfinite && X >= -126 && X <= 69) {
+    int l[WS_ND];
+#pragma unroll
+    for (int L = 0; L < WS_ND; ++L) l[L] = __float2int_rn(__uint_as_float(v[L][c]));
+    const long long shi = (long long)(l[0] * 256 + l[1]) * 65536 + (long long)(l[2] * 256 + l[3]);
+    const long long slo = (long long)l[4] * 65536 + (long long)(l[5] * 256 + l[6]);
+    const long long U = shi * 16384 + ((slo + 512) >> 10);
+    // U = U_h 2^34 + U_m 2^10 + (0 .. 2^10): both parts exact in FP32 (|U| < 2^58)
+    const float fh = __int2float_rn((int)(U >> 34));
+    const float fm = __int2float_rn((int)((U >> 10) & 0xFFFFFFll));
+    float hs, he;
+    eft_two_sum(fh * 17179869184.f, fm * 1024.f, hs, he);
+    const float p = __int_as_float((X + 127) << 23);
+    return mkdf(hs * p, he * p);
+  }
+  const double y = ws_combine(v, c, Eb, Fb, sh);
+  const float h = __double2float_rn(y);
+  return mkdf(h, isfinite(h) ? __double2float_rn(y - (double)h) : 0.f);
+}
+
 // Y(:, 0:r) = W V(:, 0:r), W rows x m FP64 (through the tensor map tmW: 128-row boxes of
-// m_max columns), V m x r FP64 (leading dimension ldV), Y rows x r FP64 (ldy).  FP64 input
+// m_max columns), V m x r (leading dimension ldV) and Y rows x r (ldy) both FP64 or both
+// float-float (VT).  FP64 input
 // read as W 2^-k with k = xr->k where xr is given (the shifted input pipeline).
+template <class VT>
 __global__ void __launch_bounds__(WS_THREADS, 1)
 k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __restrict__ m_ptr,
-          int m_val, const double* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
-          double* __restrict__ Y, int64_t ldy, int m_max, int* status, const XRange* xr) {
+          int m_val, const VT* __restrict__ V, int ldV, const int* __restrict__ r_ptr, int r_val,
+          VT* __restrict__ Y, int64_t ldy, int m_max, int* status, const XRange* xr) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int m = m_ptr ? *m_ptr : m_val;
   const int sh = xr ? xr->k : 0;
@@ -350,7 +389,7 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
   for (int j = warp; j < WS_NN; j += WS_WARPS) {
     uint32_t mx = 0;
     if (j < r)
-      for (int k = lane; k < m; k += 32) mx = max(mx, (uint32_t)__double2hiint(V[k + (size_t)j * ldV]) & 0x7FFFFFFFu);
+      for (int k = lane; k < m; k += 32) mx = max(mx, (uint32_t)__double2hiint(ws_f64(V[k + (size_t)j * ldV])) & 0x7FFFFFFFu);
 #pragma unroll
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) Fe[j] = ws_scale_exp(mx);
@@ -362,7 +401,7 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int k = 8 * kg + c;
-      x[c] = (n < r && k < m) ? V[k + (size_t)n * ldV] : 0.0;
+      x[c] = (n < r && k < m) ? ws_f64(V[k + (size_t)n * ldV]) : 0.0;
     }
     uint32_t dd[4][WS_ND];
     ws_digits8(x, Fe[n], false, dd);
@@ -514,7 +553,7 @@ k_tsmm_ws(const __grid_constant__ CUtensorMap tmW, int64_t rows, const int* __re
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const int j = 8 * half + c;
-            if (j < r) Y[row + (int64_t)j * ldy] = ws_combine(v, c, Eb, Fe[j], sh);
+            if (j < r) Y[row + (int64_t)j * ldy] = ws_out<VT>(v, c, Eb, Fe[j], sh);
           }
         }
       }
@@ -546,10 +585,13 @@ PFN_cuTensorMapEncodeTiled_v12000 ws_encoder() {
 
 }  // namespace
 
-// usable for these formats and sizes ("tsmm.ws": 0 never, 1 for the native FP64 form)
+// usable for these formats and sizes ("tsmm.ws": 0 never, 1 for an FP64 W with FP64 V and Y
+// (native FP64 arithmetic, or the float-float form's stand-alone product) or float-float V
+// and Y (the float-float form's first product, W = X))
 bool tsmm_ws_ok(Fmt in, Fmt comp, Fmt vfmt, Fmt out, int m_max, int r_max) {
   if (tune_get("tsmm.ws", 1) == 0) return false;
-  if (in != Fmt::F64 || comp != Fmt::F64 || vfmt != Fmt::F64 || out != Fmt::F64) return false;
+  if (in != Fmt::F64 || (comp != Fmt::F64 && comp != Fmt::DF) || vfmt != out) return false;
+  if (vfmt != Fmt::F64 && !(vfmt == Fmt::DF && comp == Fmt::DF)) return false;
   if (m_max < 16 || m_max > WS_MAXM || r_max < 1 || r_max > WS_NN) return false;
   return ws_smem(m_max) <= 227 * 1024;
 }
@@ -564,7 +606,7 @@ cudaError_t launch_tsmm_ws(const TsmmCfg& c, const void* W, int64_t rows, int64_
                            const void* V, int ldV, const int* r_dev, void* Y, int64_t ldy, int* status,
                            cudaStream_t s, bool* used) {
   *used = false;
-  if (c.in != Fmt::F64 || c.out != Fmt::F64 || c.vfmt != Fmt::F64) return cudaErrorInvalidValue;
+  if (c.in != Fmt::F64 || c.out != c.vfmt || (c.vfmt != Fmt::F64 && c.vfmt != Fmt::DF)) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(W) & 15) != 0 || (ld & 1) != 0 || rows < WS_TR || rows >= (1ll << 31) ||
       ld < rows)
     return cudaSuccess;
@@ -580,12 +622,19 @@ cudaError_t launch_tsmm_ws(const TsmmCfg& c, const void* W, int64_t rows, int64_
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaSuccess;
   const size_t smem = ws_smem(c.m_max);
-  cudaError_t e = cudaFuncSetAttribute(k_tsmm_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const bool dfv = c.vfmt == Fmt::DF;
+  cudaError_t e = dfv ? cudaFuncSetAttribute(k_tsmm_ws<df>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                      : cudaFuncSetAttribute(k_tsmm_ws<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (rows + WS_TR - 1) / WS_TR;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, c.ctas));
-  k_tsmm_ws<<<grid, WS_THREADS, smem, s>>>(tm, rows, m_dev, c.m_max, static_cast<const double*>(V), ldV, r_dev,
-                                           c.r_max, static_cast<double*>(Y), ldy, c.m_max, status, c.xr);
+  if (dfv)
+    k_tsmm_ws<df><<<grid, WS_THREADS, smem, s>>>(tm, rows, m_dev, c.m_max, static_cast<const df*>(V), ldV, r_dev,
+                                                 c.r_max, static_cast<df*>(Y), ldy, c.m_max, status, c.xr);
+  else
+    k_tsmm_ws<double><<<grid, WS_THREADS, smem, s>>>(tm, rows, m_dev, c.m_max, static_cast<const double*>(V), ldV,
+                                                     r_dev, c.r_max, static_cast<double*>(Y), ldy, c.m_max, status,
+                                                     c.xr);
   *used = true;
   return cudaGetLastError();
 }

@@ -132,3 +132,41 @@ def test_ws_equals_ozaki_kernel_and_unaligned_fallback():
     Wd.copy_(torch.from_numpy(np.ascontiguousarray(W.T)))
     Yu = api.tsmm(Wd, torch.from_numpy(V).cuda(), k, arith="f64").t().cpu().numpy()
     assert np.max(np.abs(Yu - Yo) / bound) <= 8 * 2.0 ** -53
+
+
+def _run_tt(X, r_max, arith):
+    from tests.gpu_common import fortran_flat
+    plan = api.TTSVDPlan(X.shape, r_max, 0.0, torch.float64, arith, want_sigma=True)
+    plan.run(fortran_flat(X))
+    return plan.result()
+
+
+@pytest.mark.parametrize("arith", ["df", "f64"])
+def test_ws_inside_tt_svd_matches_oracle_and_ozaki_kernel(arith):
+    # the whole TT-SVD with the pipeline as its first products (float-float V and Y in the
+    # float-float form, FP64 in the native form) against the Alg. 1 oracle, and against the
+    # same plan with the mma.sync Ozaki kernel
+    from oracle import tt_svd_oracle as O
+    from paper_2102_00104_gb300.inputs import uniform_tensor
+    X = uniform_tensor((8,) * 7, seed=21)
+    res = _run_tt(X, 8, arith)
+    capi.tt_tune_set("tsmm.ws", 0)
+    try:
+        res_oz = _run_tt(X, 8, arith)
+    finally:
+        capi.tt_tune_set("tsmm.ws", 1)
+    ref = O.tt_svd(X, 8)
+    assert res.ranks == ref.ranks == res_oz.ranks
+    smax = max(s[0] for s in ref.sigmas.values())
+    bar = 1e-10 if arith == "df" else 1e-12
+    for i, s in ref.sigmas.items():
+        g, go = res.sigma.get(i), res_oz.sigma.get(i)
+        if g is None or torch.isnan(g).any():
+            continue
+        k = ref.ranks[i - 1]
+        assert np.max(np.abs(g.cpu().numpy()[:k] - s[:k])) <= bar * smax
+        assert np.max(np.abs(g.cpu().numpy()[:k] - go.cpu().numpy()[:k])) <= bar * smax
+    nx = np.linalg.norm(X)
+    err = np.linalg.norm(O.tt_full(res.core_arrays()) - X) / nx
+    err_ref = np.linalg.norm(O.tt_full(ref.cores) - X) / nx
+    assert abs(err - err_ref) <= bar
