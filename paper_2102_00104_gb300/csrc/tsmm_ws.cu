@@ -15,22 +15,23 @@
 //                the previous tile);
 //   epilogue     (four warps, one per tensor-memory lane quarter) reads the seven levels
 //                back with tcgen05.ld, combines them in integer arithmetic and writes Y
-//                rounded once to FP64.
+//                (FP64 rounded once, or float-float).
 //
 // Splitting (an Ozaki scheme: Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012, with
 // integer digits): row i of W is scaled by a power of two above its largest entry,
-// v = W_ik 2^(1085 - E_i) as a 64-bit integer, E_i the largest biased exponent field of the
-// row, raised by one where that entry is within 2^-8 of the next power of two, so that
-// |v| < 2^63 - 2^55.  v is cut into balanced base-256 digits by adding C = 0x8080808080808080:
-// the bytes 7..1 of v + C, each less 128, are digits d_0..d_6 in [-128, 128) with
-// v = sum_a d_a 2^(56 - 8a) up to the dropped byte (|error| <= 2^7 + 1, 2^-55 of the row's
-// largest entry).  A digit is made as the FP16 number (1024 + byte) - 1152, exactly.  V's
-// columns are cut the same way.  A product of two digits is at most 2^14 in magnitude; a
-// level L = a + b sums at most 7 x 64 of them, below 2^23, so the FP32 accumulation of the
-// tensor cores is exact.  The levels L = 0..6 are kept (28 digit products), the result is
+// |v| = |W_ik| 2^(1085 - E_i) as a 64-bit integer, E_i the largest biased exponent field of
+// the row, raised by one where that entry is within 2^-8 of the next power of two, so that
+// |v| < 2^63 - 2^55.  |v| is cut into balanced base-256 digits by adding
+// C = 0x8080808080808080: the bytes 7..1 of |v| + C, each less 128, are digits d_0..d_6 in
+// [-128, 128) with |v| = sum_a d_a 2^(56 - 8a) up to the dropped byte (|error| <= 2^7 + 1,
+// 2^-55 of the row's largest entry); the digits of a negative entry are these negated.  A
+// digit is made as s ((1024 + byte) - 1152) by one FP16 fused multiply-add, s the sign.
+// V's columns are cut the same way.  A product of two digits is at most 2^14 in magnitude;
+// a level L = a + b sums at most 7 x 64 of them, below 2^23, so the FP32 accumulation of
+// the tensor cores is exact.  The levels L = 0..6 are kept (28 digit products), the result
+// is
 //     Y_ij = 2^(E_i + F_j - 2106) sum_L acc_L 2^(48 - 8L),
-// formed as a 64-bit integer and converted to FP64 with one rounding by integer operations
-// (the FP64 pipe of this part is slow; the epilogue does not use it).
+// formed as a 64-bit integer and rounded once to FP64 (or cut into a float-float pair).
 //
 // Every wait is bounded; a role whose wait runs out raises the CTA's abort flag, every other
 // role leaves its loop at its next wait, the bulk copies and MMAs in flight are waited for
